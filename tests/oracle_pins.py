@@ -1,0 +1,291 @@
+"""Pins for the float64 oracle: checks against what the paper and the mathematics fix.
+
+Each ``pin_*`` function returns the worst relative error it observed; the
+tests assert a bound on it, and the mutation tests assert that a planted
+mistake in the oracle drives at least one pin over its bound.  None of these
+re-types the oracle's formula: they use brute-force sums, numpy.fft (a library
+routine), exact closed forms, finite differences and invariants.
+"""
+
+import cmath
+import math
+
+import numpy as np
+
+import oracle
+from oracle import closed_forms as cf
+from paper_2412_12308_gb300 import workloads as wl
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    den = float(np.linalg.norm(b.ravel()))
+    return float(np.linalg.norm((a - b).ravel())) / (den if den > 0 else 1.0)
+
+
+# ----------------------------------------------------------------- transforms
+def brute_dft2(p):
+    """O(N^4) direct 2D sum with one combined exponential (Eq. 2D_DFT, sign -1)."""
+    ny, nx = p.shape
+    out = np.zeros((ny, nx), dtype=np.complex128)
+    for b in range(ny):
+        for a in range(nx):
+            s = 0j
+            for k in range(ny):
+                for j in range(nx):
+                    s += complex(p[k, j]) * cmath.exp(-2j * math.pi * (a * j / nx + b * k / ny))
+            out[b, a] = s
+    return out
+
+
+def pin_bruteforce(shapes=((1, 1), (2, 3), (4, 4), (5, 7), (8, 6), (3, 16), (12, 10))):
+    rng = np.random.default_rng(1)
+    worst = 0.0
+    for ny, nx in shapes:
+        p = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+        worst = max(worst, rel(oracle.dft2(p), brute_dft2(p)))
+    return worst
+
+
+def pin_numpy_fft(shapes=((64, 64), (96, 80), (160, 128), (256, 320), (30, 42))):
+    rng = np.random.default_rng(2)
+    worst = 0.0
+    for ny, nx in shapes:
+        p = rng.standard_normal((ny, nx))
+        worst = max(worst, rel(oracle.dft2(p), np.fft.fft2(p)))
+        P = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+        worst = max(worst, rel(oracle.idft2(P), np.fft.ifft2(P)))
+    return worst
+
+
+def pin_roundtrip(shapes=((64, 64), (48, 40), (128, 96))):
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    for ny, nx in shapes:
+        p = rng.standard_normal((ny, nx))
+        worst = max(worst, rel(oracle.idft2(oracle.dft2(p)), p))
+    return worst
+
+
+def pin_parseval(shapes=((64, 64), (40, 96))):
+    rng = np.random.default_rng(4)
+    worst = 0.0
+    for ny, nx in shapes:
+        p = rng.standard_normal((ny, nx))
+        lhs = float(np.sum(p * p))
+        rhs = float(np.sum(np.abs(oracle.dft2(p)) ** 2)) / (nx * ny)
+        worst = max(worst, abs(lhs - rhs) / lhs)
+    return worst
+
+
+def pin_single_mode(n=24):
+    """x_j = exp(+2 pi i a0 j / N) transforms (sign -1) to N at index a0 only."""
+    worst = 0.0
+    for a0 in (0, 1, 5, n // 2, n - 1):
+        x = np.exp(2j * np.pi * a0 * np.arange(n) / n)
+        want = np.zeros(n, dtype=np.complex128)
+        want[a0] = n
+        worst = max(worst, rel(oracle.dft1(x, sign=-1), want))
+    return worst
+
+
+# ----------------------------------------------------------------- Poisson
+def pin_poisson_modes(seed=12308, n=64):
+    f, modes, (lx, ly) = wl.poisson_modes_64(seed, n)
+    u = oracle.poisson(f, lx, ly)
+    return rel(u, cf.poisson_modes(modes, n, n, lx, ly))
+
+
+def pin_poisson_sinsin(n=32):
+    """f = sin(2 pi x) sin(2 pi y) on [0,1)^2 has lap u = f for u = -f / (8 pi^2)."""
+    x = np.arange(n) / n
+    f = np.sin(2 * np.pi * x)[None, :] * np.sin(2 * np.pi * x)[:, None]
+    return rel(oracle.poisson(f, 1.0, 1.0), -f / (8.0 * np.pi**2))
+
+
+def pin_poisson_rect(nx=48, ny=20, lx=3.0, ly=0.5):
+    """Non-square grid and domain: f = cos(2 pi (2x/Lx + 3y/Ly)), u = -f/|w|^2."""
+    x = lx * np.arange(nx) / nx
+    y = ly * np.arange(ny) / ny
+    f = np.cos(2 * np.pi * (2 * x[None, :] / lx + 3 * y[:, None] / ly))
+    w2 = (2 * np.pi * 2 / lx) ** 2 + (2 * np.pi * 3 / ly) ** 2
+    return rel(oracle.poisson(f, lx, ly), -f / w2)
+
+
+def pin_poisson_nyquist(n=16, length=2.0):
+    """The Nyquist mode (-1)^j along x is kept with |omega| = pi N / L."""
+    f = np.tile(((-1.0) ** np.arange(n))[None, :], (n, 1))
+    w2 = (np.pi * n / length) ** 2
+    return rel(oracle.poisson(f, length, length), -f / w2)
+
+
+def pin_poisson_fd(n=128, length=4.0, sigma=0.1):
+    """Gaussian source of Sec. III.A on [-2,2]^2: an 8th-order finite-difference
+    Laplacian of u must reproduce f - mean(f)."""
+    h = length / n
+    x = -length / 2 + h * np.arange(n)
+    r2 = x[None, :] ** 2 + x[:, None] ** 2
+    f = np.exp(-r2 / sigma**2)
+    u = oracle.poisson(f, length, length)
+    c = [-205.0 / 72, 8.0 / 5, -1.0 / 5, 8.0 / 315, -1.0 / 560]
+    lap = 2 * c[0] * u
+    for m in range(1, 5):
+        lap = lap + c[m] * (np.roll(u, m, 0) + np.roll(u, -m, 0) + np.roll(u, m, 1) + np.roll(u, -m, 1))
+    lap /= h * h
+    return rel(lap, f - f.mean())
+
+
+def pin_poisson_invariants(seed=7, n=40):
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((n, n))
+    u = oracle.poisson(f, 1.0, 1.0)
+    u2 = oracle.poisson(f + 3.25, 1.0, 1.0)
+    mean_err = abs(float(u.mean())) / float(np.abs(u).max())
+    return max(mean_err, rel(u2, u))
+
+
+# ----------------------------------------------------------------- diffusion
+def pin_diffusion_mode(n=32, D=0.01, t=0.7):
+    modes = [(3, -2, 1.0, 0.4), (0, 5, -0.5, 1.1)]
+    u0 = wl.mode_sum(modes, n, n, 1.0, 1.0)
+    got = oracle.diffusion(u0, D, t, 1.0, 1.0)
+    want = np.zeros_like(u0)
+    for kx, ky, amp, phi in modes:
+        w2 = (2 * np.pi) ** 2 * (kx * kx + ky * ky)
+        want += math.exp(-D * w2 * t) * wl.mode_sum([(kx, ky, amp, phi)], n, n, 1.0, 1.0)
+    return rel(got, want)
+
+
+def pin_diffusion_gaussian(n=256, D=0.1, t=1.0, seed=5):
+    """Heat-kernel evolution of periodic Gaussians on [0, 2 pi)^2."""
+    rng = np.random.default_rng(seed)
+    lx = 2 * math.pi
+    blobs = [(float(rng.uniform(0, lx)), float(rng.uniform(0, lx)), float(rng.uniform(0.15, 0.3)),
+              float(rng.standard_normal())) for _ in range(4)]
+    u0 = wl.periodic_gaussians(blobs, n, n, lx, lx)
+    got = oracle.diffusion(u0, D, t, lx, lx)
+    return rel(got, cf.gaussian_heat(blobs, D, t, n, n, lx, lx))
+
+
+def pin_diffusion_invariants(n=48, D=0.05, seed=8):
+    rng = np.random.default_rng(seed)
+    u0 = rng.standard_normal((n, n)) + 0.7
+    worst = rel(oracle.diffusion(u0, D, 0.0, 1.0, 1.0), u0)  # t = 0 is the identity
+    for t in (0.1, 1.0, 10.0):
+        u = oracle.diffusion(u0, D, t, 1.0, 1.0)
+        worst = max(worst, abs(u.mean() / u0.mean() - 1.0))  # mean conserved
+    u1 = oracle.diffusion(u0, D, 0.3, 1.0, 1.0)
+    worst = max(worst, rel(oracle.diffusion(u1, D, 0.4, 1.0, 1.0), oracle.diffusion(u0, D, 0.7, 1.0, 1.0)))
+    return worst
+
+
+def pin_diffusion_fd_time(n=32, D=0.2, t=0.05, dt=1e-5, seed=9):
+    """du/dt = D lap u: the central time difference of u, Poisson-inverted and
+    divided by D, gives u - mean(u) (O(dt^2) accurate)."""
+    rng = np.random.default_rng(seed)
+    u0 = wl.mode_sum(wl.draw_modes(rng, 6, 5), n, n, 1.0, 1.0)
+    up = oracle.diffusion(u0, D, t + dt, 1.0, 1.0)
+    um = oracle.diffusion(u0, D, t - dt, 1.0, 1.0)
+    u = oracle.diffusion(u0, D, t, 1.0, 1.0)
+    dudt = (up - um) / (2 * dt)
+    return rel(oracle.poisson(dudt / D, 1.0, 1.0), u - u.mean())
+
+
+# ----------------------------------------------------------------- wave
+def pin_wave_mode(n=32, c=1.3, t=0.37):
+    modes = [(2, 1, 0.8, 0.2), (-3, 4, 0.3, 2.0)]
+    u0 = wl.mode_sum(modes, n, n, 1.0, 1.0)
+    u, v = oracle.wave(u0, None, c, t, 1.0, 1.0, want_v=True)
+    wu = np.zeros_like(u0)
+    wv = np.zeros_like(u0)
+    for kx, ky, amp, phi in modes:
+        w = 2 * np.pi * math.sqrt(kx * kx + ky * ky)
+        m = wl.mode_sum([(kx, ky, amp, phi)], n, n, 1.0, 1.0)
+        wu += math.cos(c * w * t) * m
+        wv += -c * w * math.sin(c * w * t) * m
+    return max(rel(u, wu), rel(v, wv))
+
+
+def pin_wave_velocity_fd(n=32, c=0.8, t=0.3, dt=1e-5, seed=10):
+    """v returned by the oracle equals the central time difference of u; the
+    initial velocity g is honoured (checked by a difference at t = 0)."""
+    rng = np.random.default_rng(seed)
+    u0 = wl.mode_sum(wl.draw_modes(rng, 5, 6), n, n, 1.0, 1.0) + 0.2
+    g0 = wl.mode_sum(wl.draw_modes(rng, 5, 6), n, n, 1.0, 1.0) - 0.1
+    up = oracle.wave(u0, g0, c, t + dt, 1.0, 1.0)
+    um = oracle.wave(u0, g0, c, t - dt, 1.0, 1.0)
+    _u, v = oracle.wave(u0, g0, c, t, 1.0, 1.0, want_v=True)
+    e1 = rel((up - um) / (2 * dt), v)
+    vp = oracle.wave(u0, g0, c, dt, 1.0, 1.0)
+    vm = oracle.wave(u0, g0, c, -dt, 1.0, 1.0)
+    e2 = rel((vp - vm) / (2 * dt), g0)
+    return max(e1, e2)
+
+
+def pin_wave_invariants(n=40, c=1.0, seed=11):
+    rng = np.random.default_rng(seed)
+    u0 = rng.standard_normal((n, n)) + 0.3
+    g0 = 0.5 * rng.standard_normal((n, n)) - 0.05
+    worst = 0.0
+    # mean conserved for g = 0; grows as mean(g) t otherwise (Eq. OmegaZero)
+    for t in (0.25, 1.0, 2.0):
+        u = oracle.wave(u0, None, c, t, 1.0, 1.0)
+        worst = max(worst, abs(u.mean() / u0.mean() - 1.0))
+        u = oracle.wave(u0, g0, c, t, 1.0, 1.0)
+        worst = max(worst, abs(u.mean() - (u0.mean() + g0.mean() * t)) / abs(u0.mean()))
+    # energy: sum v^2 + c^2 |grad u|^2, with the gradient energy from a 2D FFT (numpy)
+    def energy(u, v):
+        U = np.fft.fft2(u)
+        k = 2 * np.pi * np.fft.fftfreq(n, 1.0 / n)
+        kk = k[None, :] ** 2 + k[:, None] ** 2
+        return float(np.sum(v * v)) + c * c * float(np.sum(kk * np.abs(U) ** 2)) / (n * n)
+    e0 = energy(u0, g0)
+    u, v = oracle.wave(u0, g0, c, 0.77, 1.0, 1.0, want_v=True)
+    worst = max(worst, abs(energy(u, v) / e0 - 1.0))
+    # time reversal: evolve (u, v) back by -t
+    ub, vb = oracle.wave(u, v, c, -0.77, 1.0, 1.0, want_v=True)
+    worst = max(worst, rel(ub, u0), rel(vb, g0))
+    # period return of a single mode
+    w = 2 * np.pi * math.sqrt(2 * 2 + 1 * 1)
+    m = wl.mode_sum([(2, 1, 1.0, 0.3)], n, n, 1.0, 1.0)
+    worst = max(worst, rel(oracle.wave(m, None, c, 2 * np.pi / (c * w), 1.0, 1.0), m))
+    return worst
+
+
+def pin_sign_independence(n=24, seed=12):
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((n, n + 8))
+    a = oracle.poisson(f, 1.0, 1.3, sign=-1)
+    b = oracle.poisson(f, 1.0, 1.3, sign=+1)
+    worst = rel(a, b)
+    a = oracle.wave(f, f * 0.5, 1.1, 0.4, 1.0, 1.3, sign=-1)
+    b = oracle.wave(f, f * 0.5, 1.1, 0.4, 1.0, 1.3, sign=+1)
+    worst = max(worst, rel(a, b))
+    a = oracle.diffusion(f, 0.01, 0.4, 1.0, 1.3, sign=-1)
+    b = oracle.diffusion(f, 0.01, 0.4, 1.0, 1.3, sign=+1)
+    return max(worst, rel(a, b))
+
+
+# name -> (function, bound)
+PINS = {
+    "bruteforce": (pin_bruteforce, 1e-13),
+    "numpy_fft": (pin_numpy_fft, 1e-13),
+    "roundtrip": (pin_roundtrip, 1e-14),
+    "parseval": (pin_parseval, 1e-13),
+    "single_mode": (pin_single_mode, 1e-13),
+    "poisson_modes": (pin_poisson_modes, 1e-12),
+    "poisson_sinsin": (pin_poisson_sinsin, 1e-13),
+    "poisson_rect": (pin_poisson_rect, 1e-13),
+    "poisson_nyquist": (pin_poisson_nyquist, 1e-13),
+    "poisson_fd": (pin_poisson_fd, 2e-3),
+    "poisson_invariants": (pin_poisson_invariants, 1e-12),
+    "diffusion_mode": (pin_diffusion_mode, 1e-12),
+    "diffusion_gaussian": (pin_diffusion_gaussian, 1e-11),
+    "diffusion_invariants": (pin_diffusion_invariants, 1e-12),
+    "diffusion_fd_time": (pin_diffusion_fd_time, 1e-6),
+    "wave_mode": (pin_wave_mode, 1e-12),
+    "wave_velocity_fd": (pin_wave_velocity_fd, 1e-6),
+    "wave_invariants": (pin_wave_invariants, 1e-11),
+    "sign_independence": (pin_sign_independence, 1e-13),
+}

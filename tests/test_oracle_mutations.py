@@ -1,0 +1,127 @@
+"""Planted mistakes in the oracle must trip at least one pin (no GPU).
+
+Each mutant replaces one oracle function with a plausibly wrong version (a
+dropped term, a wrong sign or index, a transposed operand) for the duration of
+the test only, on the CPU, and the pins are re-run.  A mutant that no pin
+catches would mean the pins do not constrain that part of the oracle.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.dft as odft
+import oracle.solve as osolve
+from tests import oracle_pins as pins
+
+
+def _no_shift_axis(n, length):
+    return (2.0 * np.pi / float(length)) * np.arange(n, dtype=np.float64)
+
+
+def _no_two_pi_axis(n, length):
+    a = np.arange(n)
+    ap = np.where(2 * a <= n, a, a - n)
+    return ap.astype(np.float64) / float(length)
+
+
+def _nyquist_negative_dropped_axis(n, length):
+    # maps the Nyquist index to 0 (a common off-by-one: a < n/2 kept, else shifted by n)
+    a = np.arange(n)
+    ap = np.where(2 * a < n, a, a - n)
+    ap = np.where(2 * a == n, 0, ap)
+    return (2.0 * np.pi / float(length)) * ap.astype(np.float64)
+
+
+def _poisson_sign(F, lx, ly):
+    ny, nx = F.shape
+    w2 = osolve.omega2(nx, ny, lx, ly)
+    U = np.zeros_like(F)
+    nz = w2 > 0
+    U[nz] = F[nz] / w2[nz]
+    return U
+
+
+def _poisson_keep_mean(F, lx, ly):
+    ny, nx = F.shape
+    w2 = osolve.omega2(nx, ny, lx, ly)
+    U = F.copy()
+    nz = w2 > 0
+    U[nz] = -F[nz] / w2[nz]
+    return U
+
+
+def _diffusion_omega_not_squared(F, D, t, lx, ly):
+    ny, nx = F.shape
+    w = np.sqrt(osolve.omega2(nx, ny, lx, ly))
+    return F * np.exp(-D * t * w)
+
+
+def _wave_g_times_omega(F, G, c, t, lx, ly):
+    ny, nx = F.shape
+    cw = c * np.sqrt(osolve.omega2(nx, ny, lx, ly))
+    U = F * np.cos(cw * t)
+    V = -cw * np.sin(cw * t) * F
+    if G is not None:
+        U = U + G * np.sin(cw * t) * cw
+        V = V + G * np.cos(cw * t)
+    return U, V
+
+
+def _wave_v_sign(F, G, c, t, lx, ly):
+    U, V = _ORIG_WAVE(F, G, c, t, lx, ly)
+    return U, -V
+
+
+def _idft2_unnormalised(P, sign=+1):
+    q = odft.dft1(P, axis=1, sign=sign)
+    return odft.dft1(q, axis=0, sign=sign)
+
+
+def _dft2_transposed(p, sign=-1):
+    px = odft.dft1(np.asarray(p), axis=0, sign=sign)
+    return odft.dft1(px, axis=1, sign=sign).T.copy() if p.shape[0] == p.shape[1] else \
+        odft.dft1(px, axis=1, sign=sign)[::-1].copy()
+
+
+def _dft1_sign_ignored(x, axis=-1, sign=-1):
+    return _ORIG_DFT1(x, axis=axis, sign=+1)
+
+
+_ORIG_DFT1 = odft.dft1
+_ORIG_WAVE = osolve.wave_spectrum
+
+MUTANTS = {
+    "omega_no_shift": [(osolve, "omega_axis", _no_shift_axis)],
+    "omega_no_2pi": [(osolve, "omega_axis", _no_two_pi_axis)],
+    "omega_nyquist_zero": [(osolve, "omega_axis", _nyquist_negative_dropped_axis)],
+    "poisson_sign": [(osolve, "poisson_spectrum", _poisson_sign)],
+    "poisson_keep_mean": [(osolve, "poisson_spectrum", _poisson_keep_mean)],
+    "diffusion_omega_not_squared": [(osolve, "diffusion_spectrum", _diffusion_omega_not_squared)],
+    "wave_g_times_omega": [(osolve, "wave_spectrum", _wave_g_times_omega)],
+    "wave_v_sign": [(osolve, "wave_spectrum", _wave_v_sign)],
+    "idft2_unnormalised": [(osolve, "idft2", _idft2_unnormalised), (oracle, "idft2", _idft2_unnormalised)],
+    "dft2_transposed": [(osolve, "dft2", _dft2_transposed), (oracle, "dft2", _dft2_transposed)],
+    "dft1_sign_ignored": [(odft, "dft1", _dft1_sign_ignored), (oracle, "dft1", _dft1_sign_ignored)],
+}
+
+
+def _failing_pins():
+    failed = []
+    for name, (fn, bound) in pins.PINS.items():
+        try:
+            err = fn()
+        except Exception:  # a crash counts as caught
+            failed.append(name)
+            continue
+        if not (err <= bound):
+            failed.append(name)
+    return failed
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS))
+def test_mutant_is_caught(mutant, monkeypatch):
+    for mod, attr, repl in MUTANTS[mutant]:
+        monkeypatch.setattr(mod, attr, repl)
+    failed = _failing_pins()
+    assert failed, f"mutant {mutant} passed every pin"
