@@ -1,0 +1,139 @@
+/*
+ * fsolve.h -- C ABI of the GB300 (sm_103a) 2D Fourier-space PDE solver.
+ *
+ * Method: arXiv:2412.12308.  A solve is a forward 2D DFT of a real field on a
+ * periodic Nx x Ny grid (Sec. II.D, row transforms along x then column
+ * transforms along y), a pointwise spectral operator (Sec. III), and the
+ * inverse 2D DFT (the inverse formula after Eq. DFT2, 1/(Nx Ny) applied once).
+ *
+ * Conventions shared by every entry point
+ *   Fields      real, row-major [ny][nx] (x fastest), element type given by
+ *               the plan's dtype (float or double), on the DEVICE, owned by the
+ *               caller.  Sample x_j = j Lx/nx, y_k = k Ly/ny (Sec. II.D).
+ *   Wavenumbers omega_x(a) = 2 pi a'/Lx, a' = a for a <= nx/2 else a - nx (the
+ *               index shift of Sec. II.B); the Nyquist index is kept with
+ *               |omega| = pi nx / Lx.  |omega|^2 = omega_x^2 + omega_y^2.
+ *   Sizes       nx, ny even, 8 <= n <= 8192, n = 2^a * {1, 3, 5}; nx != ny and
+ *               Lx != Ly allowed.  Anything else: FS_ERR_SIZE.
+ *   Streams     fs_stream is a cudaStream_t (NULL = legacy default stream).
+ *               Every call only enqueues work on that stream and returns; none
+ *               synchronises except fs_serve_poll (bounded by its timeout).
+ *   Workspace   a plan owns its device workspace (twiddle and wavenumber
+ *               tables, one half-spectrum); calls on one plan (or on states of
+ *               one plan) must be ordered on one stream.  Different plans are
+ *               independent.
+ *   Errors      every entry point returns fs_status; nothing is thrown across
+ *               the ABI.  fs_last_error() returns a thread-local message for
+ *               the last failing call on the calling thread.  A CUDA error
+ *               raised while enqueuing returns FS_ERR_CUDA; asynchronous kernel
+ *               faults surface at the caller's next synchronisation.
+ *   Precision   FS_F32: float fields, FP32 butterflies with twiddles computed
+ *               in FP64 and rounded once; spectral factors combined in
+ *               double-float (two-float) arithmetic and rounded once.
+ *               Target: rel-L2 <= 1e-5 against an FP64 reference.
+ *               FS_F64: everything in FP64, target rel-L2 <= 1e-12.
+ */
+#ifndef FSOLVE_H
+#define FSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fs_plan_s *fs_plan;
+typedef struct fs_state_s *fs_state;
+typedef void *fs_stream;
+
+typedef enum { FS_F32 = 0, FS_F64 = 1 } fs_dtype;
+
+typedef enum {
+  FS_OK = 0,
+  FS_ERR_ARG = -1,     /* null handle/pointer, bad enum, negative time */
+  FS_ERR_SIZE = -2,    /* unsupported grid size */
+  FS_ERR_NOMEM = -3,   /* device or host allocation failed */
+  FS_ERR_BUDGET = -4,  /* request does not fit the serving HBM budget */
+  FS_ERR_CUDA = -5,    /* a CUDA runtime call failed */
+  FS_ERR_TIMEOUT = -6, /* a bounded device wait or fs_serve_poll timed out */
+  FS_ERR_BUSY = -7,    /* resource in use (e.g. serving queue full) */
+  FS_ERR_NODEV = -8    /* no CUDA device visible */
+} fs_status;
+
+/* ---------------------------------------------------------------- plans
+ * fs_plan_create: validate (nx, ny), build the radix factorisation of nx/2
+ * and ny, the FP64-generated twiddle tables omega_N^m (Eq. DFT) rounded once to
+ * the plan dtype, the per-axis |omega|^2 tables (Sec. II.D frequency grid with
+ * the Sec. II.B shift), and allocate the plan's workspace on the current
+ * device.  dtype is an fs_dtype.  *out receives the handle (library-owned;
+ * release with fs_plan_destroy).  Errors: FS_ERR_ARG (out NULL, Lx/Ly <= 0,
+ * bad dtype), FS_ERR_SIZE, FS_ERR_NOMEM, FS_ERR_NODEV, FS_ERR_CUDA.
+ */
+fs_status fs_plan_create(int nx, int ny, double lx, double ly, int dtype, fs_plan *out);
+/* Frees the plan's device memory after synchronising the device. NULL is ok. */
+fs_status fs_plan_destroy(fs_plan plan);
+/* Query: grid and path of a plan. path: 0 = single-kernel shared-memory solve,
+ * 1 = three-pass (row / fused column / row). Any out pointer may be NULL. */
+fs_status fs_plan_info(fs_plan plan, int *nx, int *ny, int *dtype, int *path,
+                       size_t *workspace_bytes);
+
+/* ---------------------------------------------------------------- one-shot solves
+ * fs_poisson_solve: u = the zero-mean solution of lap u = f - mean(f)
+ * (Eq. Poisson2, Eq. SolutionPoisson): forward 2D DFT, multiply by
+ * -1/|omega|^2 with the zero mode set to 0, inverse 2D DFT.  f and u are device
+ * [ny][nx] arrays of the plan dtype; u may alias f.
+ */
+fs_status fs_poisson_solve(fs_plan plan, const void *f, void *u, fs_stream stream);
+
+/* fs_diffusion_solve: u(t) of u_t = D lap u from u(0) = u0 (Eq. DiffusionIVPFS
+ * with s = 0, Eq. solCalorFourier; D rescales time): multiplier
+ * exp(-D |omega|^2 t).  D >= 0, t >= 0.  u may alias u0. */
+fs_status fs_diffusion_solve(fs_plan plan, const void *u0, double D, double t, void *u,
+                             fs_stream stream);
+
+/* fs_wave_solve: u(t) of u_tt = c^2 lap u from u(0) = u0, u_t(0) = v0
+ * (Eq. WaveEquationFourierSpace with s = 0; Eq. OmegaZero, Eq. OmegaNonZero
+ * with t -> c t).  v0 may be NULL (zero initial velocity).  c > 0; t may be
+ * negative (the solution operator is a group).  u may alias u0. */
+fs_status fs_wave_solve(fs_plan plan, const void *u0, const void *v0, double c, double t,
+                        void *u, fs_stream stream);
+
+/* ---------------------------------------------------------------- kept states
+ * fs_state_create: forward-transform the initial data once and keep the
+ * half-spectra U0 (and V0 when v0 != NULL) on the device (Sec. III.B/III.C:
+ * the IVP in Fourier space is fixed by f-hat and g-hat).  u0, v0: device
+ * [ny][nx] of the plan dtype, read during the call's stream work only.  The
+ * state is library-owned; release with fs_state_destroy.
+ */
+fs_status fs_state_create(fs_plan plan, const void *u0, const void *v0, fs_stream stream,
+                          fs_state *out);
+fs_status fs_state_destroy(fs_state state);
+
+/* fs_diffusion_advance: u(t) from a kept state, t absolute (>= 0) from the
+ * state's initial data: inverse 2D DFT of U0 exp(-D|omega|^2 t)
+ * (Eq. solCalorFourier).  u_out: device [ny][nx]. */
+fs_status fs_diffusion_advance(fs_state state, double D, double t, void *u_out, fs_stream stream);
+
+/* fs_wave_advance: u(t) (and v = u_t(t) when v_out != NULL) from a kept state:
+ * U = U0 cos(c|omega|t) + V0 sin(c|omega|t)/(c|omega|), U = U0 + V0 t at
+ * omega = 0 (Eq. OmegaZero/OmegaNonZero); V = -c|omega| U0 sin + V0 cos (the
+ * first-order system, Eq. SystemOfODEsForWaveEquation). */
+fs_status fs_wave_advance(fs_state state, double c, double t, void *u_out, void *v_out,
+                          fs_stream stream);
+
+/* ---------------------------------------------------------------- misc */
+const char *fs_last_error(void);
+/* Size rule used by every entry point: 1 if n is supported, else 0. */
+int fs_size_supported(int n);
+/* Radix factorisation used for a length-L transform with `e` elements per
+ * thread: writes up to `cap` radices into out, returns the count (0: none). */
+int fs_radix_plan(int L, int e, int *out, int cap);
+/* Number of this library's kernels launched since load (all threads). */
+uint64_t fs_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSOLVE_H */

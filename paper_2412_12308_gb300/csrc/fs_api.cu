@@ -1,0 +1,507 @@
+// fs_api.cu -- plans, kept states and the one-shot / advance entry points of
+// the C ABI (include/fsolve.h).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "fs_host.h"
+#include "fs_kernels.cuh"
+
+// The kernels are instantiated in fs_kernels_f32.cu / fs_kernels_f64.cu.
+extern template struct fs::Launch<float>;
+extern template struct fs::Launch<double>;
+
+namespace fs {
+
+std::atomic<unsigned long long> g_launches{0};
+
+static thread_local std::string t_last_error;
+
+fs_status set_error(fs_status st, const std::string &msg) {
+  t_last_error = msg;
+  return st;
+}
+
+fs_status cuda_error(cudaError_t e, const char *what) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return set_error(FS_ERR_NOMEM, buf);
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return set_error(FS_ERR_NODEV, buf);
+  return set_error(FS_ERR_CUDA, buf);
+}
+
+bool size_supported(int n) {
+  if (n < 8 || n > 8192 || (n & 1)) return false;
+  int m = n;
+  while ((m & 1) == 0) m >>= 1;
+  return m == 1 || m == 3 || m == 5;
+}
+
+// Elements per thread: the first register tile of the size's family (in
+// preference order) that divides L with at most 512 threads per transform.
+// FP64 prefers half-size tiles (twice the registers per element).
+int choose_e(int L, bool f64) {
+  int m = L;
+  while ((m & 1) == 0) m >>= 1;
+  static const int pow2[] = {16, 8, 4}, three[] = {24, 12, 6}, five[] = {20, 10, 5};
+  static const int pow2d[] = {8, 4, 16}, threed[] = {12, 6, 24}, fived[] = {10, 5, 20};
+  const int *cand = m == 1 ? (f64 ? pow2d : pow2)
+                           : (m == 3 ? (f64 ? threed : three) : (m == 5 ? (f64 ? fived : five) : nullptr));
+  if (!cand) return 0;
+  for (int i = 0; i < 3; ++i) {
+    const int e = cand[i];
+    if (L >= e && L % e == 0 && L / e <= kMaxThreads) return e;
+  }
+  return 0;
+}
+
+// Radices dividing e, power-of-two stages largest first, then the odd stage.
+int radix_plan(int L, int e, int *out, int cap) {
+  if (L <= 0 || e <= 0) return 0;
+  int odd = L, p2 = 1;
+  while ((odd & 1) == 0) {
+    odd >>= 1;
+    p2 <<= 1;
+  }
+  if (odd != 1 && odd != 3 && odd != 5) return 0;
+  if (odd > 1 && e % odd) return 0;
+  int n = 0;
+  static const int rs[] = {16, 8, 4, 2};
+  while (p2 > 1) {
+    int pick = 0;
+    for (int r : rs)
+      if (e % r == 0 && p2 % r == 0) {
+        pick = r;
+        break;
+      }
+    if (!pick || n >= cap) return 0;
+    out[n++] = pick;
+    p2 /= pick;
+  }
+  if (odd > 1) {
+    if (n >= cap) return 0;
+    out[n++] = odd;
+  }
+  return n;
+}
+
+static bool make_rp(int L, bool f64, RadixPlan *rp) {
+  memset(rp, 0, sizeof *rp);
+  rp->e = choose_e(L, f64);
+  if (!rp->e) return false;
+  rp->n = radix_plan(L, rp->e, rp->r, 8);
+  return rp->n > 0;
+}
+
+static int env_int(const char *name, int dflt) {
+  const char *v = getenv(name);
+  return v && *v ? atoi(v) : dflt;
+}
+
+// Tile shapes: row tiles of up to 16 rows (longer contiguous runs in the
+// x-frequency-major spectrum), column groups of up to 32 columns, at most 512
+// threads and ~96 KB of exchange scratch per CTA.
+static TileConfig make_tiles(int nx, int ny, const RadixPlan &rr, const RadixPlan &rc, size_t cs) {
+  TileConfig t{};
+  const int M = nx / 2;
+  const int tr = M / rr.e, tcl = ny / rc.e;
+  const size_t lim = 96 * 1024;
+  int cr = 16;
+  while (cr > 1 && (cr * tr > kMaxThreads || cs * padded_len(cr * M) > lim)) cr >>= 1;
+  if (cr > ny) cr = ny;
+  t.rows_per_unit = cr;
+  int cc = 32;
+  while (cc > 1 && (cc * tcl > kMaxThreads || cs * padded_len(cc * ny) > lim)) cc >>= 1;
+  t.cols_per_unit = cc;
+  // small path: whole half spectrum resident in shared memory
+  int sr = ny < kMaxThreads / tr ? ny : kMaxThreads / tr;
+  int sc = (M + 1) < kMaxThreads / tcl ? (M + 1) : kMaxThreads / tcl;
+  if (sr < 1) sr = 1;
+  if (sc < 1) sc = 1;
+  const size_t spec = (size_t)(M + 1) * ny;
+  const size_t smem_lim = (size_t)env_int("FS_SMALL_SMEM_MAX", 200 * 1024);
+  auto fit = [&](int nspec, int &r, int &c) -> size_t {
+    for (;;) {
+      const size_t x = (size_t)(padded_len(r * M) > padded_len(c * ny) ? padded_len(r * M)
+                                                                       : padded_len(c * ny));
+      const size_t b = cs * (spec * nspec + x);
+      if (b <= smem_lim) return b;
+      if (r > 1 && r * M >= c * ny) r = (r + 1) / 2;
+      else if (c > 1) c = (c + 1) / 2;
+      else return 0;
+      if (cs * spec * nspec > smem_lim) return 0;
+    }
+  };
+  int r1 = sr, c1 = sc;
+  t.small_smem1 = fit(1, r1, c1);
+  int r2 = r1, c2 = c1;
+  t.small_smem2 = t.small_smem1 ? fit(2, r2, c2) : 0;
+  // one row/column grouping for both variants (results must not depend on it)
+  t.small_rows = t.small_smem2 ? r2 : r1;
+  t.small_cols = t.small_smem2 ? c2 : c1;
+  if (t.small_smem2) t.small_smem1 = cs * (spec + (size_t)(padded_len(r2 * M) > padded_len(c2 * ny)
+                                                              ? padded_len(r2 * M)
+                                                              : padded_len(c2 * ny)));
+  return t;
+}
+
+Desc base_desc(const fs_plan_s *p) {
+  Desc d;
+  memset(&d, 0, sizeof d);
+  d.nx = p->nx;
+  d.ny = p->ny;
+  d.M = p->M;
+  d.rows_per_unit = p->tc.rows_per_unit;
+  d.cols_per_unit = p->tc.cols_per_unit;
+  d.n_row_units = (p->ny + d.rows_per_unit - 1) / d.rows_per_unit;
+  d.n_col_units = (p->M + 1 + d.cols_per_unit - 1) / d.cols_per_unit;
+  d.n_fac_units = (p->M + 1 + p->ny + kFactorPerUnit - 1) / kFactorPerUnit;
+  d.small_rows = p->tc.small_rows;
+  d.small_cols = p->tc.small_cols;
+  d.rp_row = p->rp_row;
+  d.rp_col = p->rp_col;
+  d.tw_x = p->tw_x;
+  d.tw_y = p->tw_y;
+  d.wx2 = p->wx2;
+  d.wy2 = p->wy2;
+  d.wx2d = p->wx2d;
+  d.wy2d = p->wy2d;
+  d.fac = p->fac;
+  d.work_u = p->work_u;
+  d.work_v = p->work_v;
+  d.scale = 1.0 / ((double)p->nx * (double)p->ny);
+  return d;
+}
+
+size_t fac_bytes(const fs_plan_s *p) {
+  return (size_t)(p->M + 1 + p->ny) * (p->dtype == FS_F64 ? sizeof(double) : sizeof(float2));
+}
+
+// Signed-index angular wavenumber squared: (2 pi a'/L)^2, a' = a (a <= n/2) else a - n.
+static double omega2_axis(int a, int n, double len) {
+  const int ap = (2 * a <= n) ? a : a - n;
+  const double w = 2.0 * M_PI * (double)ap / len;
+  return w * w;
+}
+
+}  // namespace fs
+
+using namespace fs;
+
+static cudaError_t alloc_dev(void **p, size_t bytes) { return cudaMalloc(p, bytes); }
+
+static fs_status ensure_work_v(fs_plan p) {
+  if (p->work_v) return FS_OK;
+  cudaError_t e = alloc_dev(&p->work_v, p->spec_bytes);
+  if (e != cudaSuccess) return cuda_error(e, "workspace allocation");
+  return FS_OK;
+}
+
+extern "C" {
+
+const char *fs_last_error(void) { return t_last_error.c_str(); }
+
+int fs_size_supported(int n) { return size_supported(n) ? 1 : 0; }
+
+int fs_radix_plan(int L, int e, int *out, int cap) { return radix_plan(L, e, out, cap); }
+
+uint64_t fs_kernel_launches(void) { return g_launches.load(); }
+
+fs_status fs_plan_create(int nx, int ny, double lx, double ly, int dtype, fs_plan *out) {
+  if (!out) return set_error(FS_ERR_ARG, "fs_plan_create: out is NULL");
+  *out = nullptr;
+  if (!(lx > 0.0) || !(ly > 0.0) || !std::isfinite(lx) || !std::isfinite(ly))
+    return set_error(FS_ERR_ARG, "fs_plan_create: Lx and Ly must be finite and > 0");
+  if (dtype != FS_F32 && dtype != FS_F64) return set_error(FS_ERR_ARG, "fs_plan_create: bad dtype");
+  if (!size_supported(nx) || !size_supported(ny)) {
+    char buf[160];
+    snprintf(buf, sizeof buf,
+             "fs_plan_create: unsupported size %d x %d (need even n = 2^a*{1,3,5}, 8 <= n <= 8192)",
+             nx, ny);
+    return set_error(FS_ERR_SIZE, buf);
+  }
+  fs_plan_s tmp;
+  memset(&tmp, 0, sizeof tmp);
+  tmp.nx = nx;
+  tmp.ny = ny;
+  tmp.M = nx / 2;
+  tmp.lx = lx;
+  tmp.ly = ly;
+  tmp.dtype = dtype;
+  if (!make_rp(tmp.M, dtype == FS_F64, &tmp.rp_row) || !make_rp(ny, dtype == FS_F64, &tmp.rp_col))
+    return set_error(FS_ERR_SIZE, "fs_plan_create: no radix plan for this size");
+  tmp.csize = dtype == FS_F64 ? 2 * sizeof(double) : 2 * sizeof(float);
+  tmp.tc = make_tiles(nx, ny, tmp.rp_row, tmp.rp_col, tmp.csize);
+  const int small_max = env_int("FS_SMALL_MAX", 128 * 128);
+  tmp.standalone_small = (nx * ny <= small_max) && tmp.tc.small_smem2 > 0;
+  tmp.spec_bytes = (size_t)(tmp.M + 1) * ny * tmp.csize;
+
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return set_error(FS_ERR_NODEV, "fs_plan_create: no CUDA device visible");
+  }
+  e = cudaGetDevice(&tmp.device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+
+  // ---- host tables in FP64
+  const bool f64 = dtype == FS_F64;
+  const int M = tmp.M;
+  std::vector<double> wx2d(M + 1), wy2d(ny);
+  for (int a = 0; a <= M; ++a) wx2d[a] = omega2_axis(a, nx, lx);
+  for (int b = 0; b < ny; ++b) wy2d[b] = omega2_axis(b, ny, ly);
+  auto twiddles = [&](int n, std::vector<unsigned char> &buf) {
+    buf.resize((size_t)n * tmp.csize);
+    for (int m = 0; m < n; ++m) {
+      const double ang = 2.0 * M_PI * (double)m / (double)n;  // exact integer m < n
+      const double c = cos(ang), s = -sin(ang);                // e^{-2 pi i m / n}
+      if (f64) {
+        double *q = reinterpret_cast<double *>(buf.data()) + 2 * m;
+        q[0] = c;
+        q[1] = s;
+      } else {
+        float *q = reinterpret_cast<float *>(buf.data()) + 2 * m;
+        q[0] = (float)c;
+        q[1] = (float)s;
+      }
+    }
+  };
+  std::vector<unsigned char> twx, twy;
+  twiddles(nx, twx);
+  twiddles(ny, twy);
+  auto axis_tab = [&](const std::vector<double> &w, std::vector<unsigned char> &buf) {
+    if (f64) {
+      buf.resize(w.size() * sizeof(double));
+      memcpy(buf.data(), w.data(), buf.size());
+    } else {
+      buf.resize(w.size() * sizeof(float2));
+      float *q = reinterpret_cast<float *>(buf.data());
+      for (size_t i = 0; i < w.size(); ++i) split_double(w[i], q[2 * i], q[2 * i + 1]);
+    }
+  };
+  std::vector<unsigned char> wxt, wyt;
+  axis_tab(wx2d, wxt);
+  axis_tab(wy2d, wyt);
+
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t o_twx = 0, o_twy = o_twx + al(twx.size()), o_wx = o_twy + al(twy.size()),
+               o_wy = o_wx + al(wxt.size()), o_wxd = o_wy + al(wyt.size()),
+               o_wyd = o_wxd + al(wx2d.size() * 8), total = o_wyd + al(wy2d.size() * 8);
+
+  fs_plan p = new (std::nothrow) fs_plan_s(tmp);
+  if (!p) return set_error(FS_ERR_NOMEM, "fs_plan_create: host allocation");
+  e = alloc_dev(&p->tables, total);
+  if (e == cudaSuccess) e = alloc_dev(&p->work_u, p->spec_bytes);
+  if (e == cudaSuccess) e = alloc_dev(&p->fac, fac_bytes(p));
+  if (e != cudaSuccess) {
+    cudaFree(p->tables);
+    cudaFree(p->work_u);
+    cudaFree(p->fac);
+    delete p;
+    return cuda_error(e, "fs_plan_create: device allocation");
+  }
+  char *base = reinterpret_cast<char *>(p->tables);
+  p->tw_x = base + o_twx;
+  p->tw_y = base + o_twy;
+  p->wx2 = base + o_wx;
+  p->wy2 = base + o_wy;
+  p->wx2d = reinterpret_cast<double *>(base + o_wxd);
+  p->wy2d = reinterpret_cast<double *>(base + o_wyd);
+  e = cudaMemcpy(p->tw_x, twx.data(), twx.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->tw_y, twy.data(), twy.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->wx2, wxt.data(), wxt.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->wy2, wyt.data(), wyt.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->wx2d, wx2d.data(), wx2d.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->wy2d, wy2d.data(), wy2d.size() * 8, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    fs_plan_destroy(p);
+    return cuda_error(e, "fs_plan_create: table upload");
+  }
+  *out = p;
+  return FS_OK;
+}
+
+fs_status fs_plan_destroy(fs_plan p) {
+  if (!p) return FS_OK;
+  cudaDeviceSynchronize();
+  cudaFree(p->tables);
+  cudaFree(p->work_u);
+  cudaFree(p->work_v);
+  cudaFree(p->fac);
+  delete p;
+  return FS_OK;
+}
+
+fs_status fs_plan_info(fs_plan p, int *nx, int *ny, int *dtype, int *path, size_t *ws) {
+  if (!p) return set_error(FS_ERR_ARG, "fs_plan_info: plan is NULL");
+  if (nx) *nx = p->nx;
+  if (ny) *ny = p->ny;
+  if (dtype) *dtype = p->dtype;
+  if (path) *path = p->standalone_small ? 0 : 1;
+  if (ws) *ws = p->spec_bytes * (p->work_v ? 2 : 1) + fac_bytes(p);
+  return FS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- dispatch
+template <typename T>
+static cudaError_t run_desc(const fs_plan_s *p, const Desc &d, cudaStream_t s) {
+  typedef Launch<T> L;
+  const bool diff = d.op == OP_DIFFUSION || d.op == OP_DIFF_ADV;
+  const bool adv = d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV;
+  const bool has_v = (d.flags & F_HAS_V0) != 0;
+  if (p->standalone_small) return L::small(d, s);
+  cudaError_t e = cudaSuccess;
+  if (diff) e = L::factor(d, s);
+  if (e == cudaSuccess && !adv) {
+    const int fields = ((d.op == OP_WAVE || d.op == OP_FORWARD) && has_v) ? 2 : 1;
+    e = L::rows(d, fields, s);
+  }
+  if (e == cudaSuccess) e = L::cols(d, s);
+  if (e == cudaSuccess && d.op != OP_FORWARD) {
+    const int fields = (d.op == OP_WAVE_ADV && (d.flags & F_WANT_V)) ? 2 : 1;
+    e = L::c2r(d, fields, s);
+  }
+  return e;
+}
+
+static fs_status run(const fs_plan_s *p, const Desc &d, fs_stream stream, const char *what) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = p->dtype == FS_F64 ? run_desc<double>(p, d, s) : run_desc<float>(p, d, s);
+  if (e != cudaSuccess) return cuda_error(e, what);
+  return FS_OK;
+}
+
+extern "C" {
+
+fs_status fs_poisson_solve(fs_plan p, const void *f, void *u, fs_stream stream) {
+  if (!p || !f || !u) return set_error(FS_ERR_ARG, "fs_poisson_solve: NULL argument");
+  Desc d = base_desc(p);
+  d.op = OP_POISSON;
+  d.in_u = f;
+  d.out_u = u;
+  return run(p, d, stream, "fs_poisson_solve");
+}
+
+fs_status fs_diffusion_solve(fs_plan p, const void *u0, double D, double t, void *u,
+                             fs_stream stream) {
+  if (!p || !u0 || !u) return set_error(FS_ERR_ARG, "fs_diffusion_solve: NULL argument");
+  if (!(D >= 0.0) || !(t >= 0.0) || !std::isfinite(D * t))
+    return set_error(FS_ERR_ARG, "fs_diffusion_solve: need finite D >= 0 and t >= 0");
+  Desc d = base_desc(p);
+  d.op = OP_DIFFUSION;
+  d.in_u = u0;
+  d.out_u = u;
+  d.p_dt = D * t;
+  d.p_t = t;
+  return run(p, d, stream, "fs_diffusion_solve");
+}
+
+fs_status fs_wave_solve(fs_plan p, const void *u0, const void *v0, double c, double t, void *u,
+                        fs_stream stream) {
+  if (!p || !u0 || !u) return set_error(FS_ERR_ARG, "fs_wave_solve: NULL argument");
+  if (!(c > 0.0) || !std::isfinite(c) || !std::isfinite(t))
+    return set_error(FS_ERR_ARG, "fs_wave_solve: need finite c > 0 and finite t");
+  if (v0 && !p->standalone_small) {
+    fs_status st = ensure_work_v(p);
+    if (st != FS_OK) return st;
+  }
+  Desc d = base_desc(p);
+  d.op = OP_WAVE;
+  d.flags = v0 ? F_HAS_V0 : 0;
+  d.in_u = u0;
+  d.in_v = v0;
+  d.out_u = u;
+  d.p_c = c;
+  d.p_t = t;
+  return run(p, d, stream, "fs_wave_solve");
+}
+
+fs_status fs_state_create(fs_plan p, const void *u0, const void *v0, fs_stream stream,
+                          fs_state *out) {
+  if (!out) return set_error(FS_ERR_ARG, "fs_state_create: out is NULL");
+  *out = nullptr;
+  if (!p || !u0) return set_error(FS_ERR_ARG, "fs_state_create: NULL argument");
+  if (v0 && !p->standalone_small) {
+    fs_status st = ensure_work_v(p);
+    if (st != FS_OK) return st;
+  }
+  fs_state s = new (std::nothrow) fs_state_s();
+  if (!s) return set_error(FS_ERR_NOMEM, "fs_state_create: host allocation");
+  s->plan = p;
+  s->has_v = v0 != nullptr;
+  cudaError_t e = alloc_dev(&s->su, p->spec_bytes);
+  if (e == cudaSuccess && v0) e = alloc_dev(&s->sv, p->spec_bytes);
+  if (e != cudaSuccess) {
+    cudaFree(s->su);
+    delete s;
+    return cuda_error(e, "fs_state_create: device allocation");
+  }
+  Desc d = base_desc(p);
+  d.op = OP_FORWARD;
+  d.flags = v0 ? F_HAS_V0 : 0;
+  d.in_u = u0;
+  d.in_v = v0;
+  d.st_out_u = s->su;
+  d.st_out_v = s->sv;
+  fs_status st = run(p, d, stream, "fs_state_create");
+  if (st != FS_OK) {
+    cudaFree(s->su);
+    cudaFree(s->sv);
+    delete s;
+    return st;
+  }
+  *out = s;
+  return FS_OK;
+}
+
+fs_status fs_state_destroy(fs_state s) {
+  if (!s) return FS_OK;
+  cudaDeviceSynchronize();
+  cudaFree(s->su);
+  cudaFree(s->sv);
+  delete s;
+  return FS_OK;
+}
+
+fs_status fs_diffusion_advance(fs_state s, double D, double t, void *u_out, fs_stream stream) {
+  if (!s || !u_out) return set_error(FS_ERR_ARG, "fs_diffusion_advance: NULL argument");
+  if (!(D >= 0.0) || !(t >= 0.0) || !std::isfinite(D * t))
+    return set_error(FS_ERR_ARG, "fs_diffusion_advance: need finite D >= 0 and t >= 0");
+  fs_plan p = s->plan;
+  Desc d = base_desc(p);
+  d.op = OP_DIFF_ADV;
+  d.st_u = s->su;
+  d.out_u = u_out;
+  d.p_dt = D * t;
+  d.p_t = t;
+  return run(p, d, stream, "fs_diffusion_advance");
+}
+
+fs_status fs_wave_advance(fs_state s, double c, double t, void *u_out, void *v_out,
+                          fs_stream stream) {
+  if (!s || !u_out) return set_error(FS_ERR_ARG, "fs_wave_advance: NULL argument");
+  if (!(c > 0.0) || !std::isfinite(c) || !std::isfinite(t))
+    return set_error(FS_ERR_ARG, "fs_wave_advance: need finite c > 0 and finite t");
+  fs_plan p = s->plan;
+  if (v_out && !p->standalone_small) {
+    fs_status st = ensure_work_v(p);
+    if (st != FS_OK) return st;
+  }
+  Desc d = base_desc(p);
+  d.op = OP_WAVE_ADV;
+  d.flags = (s->has_v ? F_HAS_V0 : 0) | (v_out ? F_WANT_V : 0);
+  d.st_u = s->su;
+  d.st_v = s->sv;
+  d.out_u = u_out;
+  d.out_v = v_out;
+  d.p_c = c;
+  d.p_t = t;
+  return run(p, d, stream, "fs_wave_advance");
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// fs_desc.h -- problem descriptor shared by host code and kernels.
+//
+// One Desc describes one solve or one advance on one grid: which operator,
+// the radix plans of the two 1D transform lengths (nx/2 for the packed real
+// row transform, ny for the column transform), the tile shapes, and every
+// device pointer the units read or write.  The same descriptor drives the
+// standalone pass kernels, the single-kernel small-grid path and the
+// persistent batch kernel, so a problem computes bit-identically on all of
+// them for a given tile shape.
+#pragma once
+#include <stdint.h>
+
+namespace fs {
+
+enum Op : int {
+  OP_POISSON = 0,     // Eq. SolutionPoisson
+  OP_DIFFUSION = 1,   // Eq. solCalorFourier, from a field
+  OP_WAVE = 2,        // Eq. OmegaZero / OmegaNonZero, from fields
+  OP_DIFF_ADV = 3,    // diffusion from a kept spectrum
+  OP_WAVE_ADV = 4,    // wave from kept spectra
+  OP_FORWARD = 5      // forward 2D DFT into kept spectra (state creation)
+};
+
+enum Flags : int {
+  F_HAS_V0 = 1,   // wave: an initial velocity field / spectrum is present
+  F_WANT_V = 2    // wave advance: also produce v = u_t
+};
+
+// Unit kinds of the persistent batch kernel, in dependency order.
+enum Kind : int { K_FACTOR = 0, K_ROW = 1, K_SMALL = 2, K_COL = 3, K_C2R = 4 };
+
+struct RadixPlan {
+  int32_t e;         // elements held per thread (the register tile)
+  int32_t n;         // number of stages
+  int32_t r[8];      // radix of each stage, product = transform length
+};
+
+struct Desc {
+  int32_t op, flags;
+  int32_t nx, ny, M;          // M = nx/2: length of the packed real row transform
+  int32_t rows_per_unit;      // row tile height of the row passes
+  int32_t cols_per_unit;      // columns per column-pass unit
+  int32_t n_row_units;        // per field
+  int32_t n_col_units;
+  int32_t n_fac_units;
+  int32_t small;              // 1: whole problem in one CTA (shared-memory resident)
+  int32_t small_rows;         // row group of the small path
+  int32_t small_cols;         // column group of the small path
+  RadixPlan rp_row;           // length M
+  RadixPlan rp_col;           // length ny
+  const void *in_u, *in_v;    // real fields [ny][nx]
+  void *out_u, *out_v;        // real fields [ny][nx]
+  void *work_u, *work_v;      // half-spectra [M+1][ny] (x-frequency major)
+  const void *st_u, *st_v;    // kept spectra (advance ops)
+  void *st_out_u, *st_out_v;  // where OP_FORWARD keeps the spectra
+  const void *tw_x, *tw_y;    // omega_nx^m (m < nx), omega_ny^m (m < ny)
+  const void *wx2, *wy2;      // |omega_x|^2 (a <= M), |omega_y|^2 (b < ny); two-float or double
+  const double *wx2d, *wy2d;  // the same in float64 (factor tables)
+  void *fac;                  // diffusion per-axis factors: x part [M+1], y part [ny]
+  double p_dt;                // D * t
+  double p_c;                 // wave speed c
+  double p_t;                 // time t
+  double scale;               // 1 / (nx * ny)
+};
+
+}  // namespace fs

@@ -1,0 +1,296 @@
+// fs_fft.cuh -- complex arithmetic, small DFT butterflies and the
+// register-resident mixed-radix FFT engine used by every kernel.
+//
+// The engine computes the length-L DFT of Sec. II.B (Eq. DFT) with the
+// even/odd splitting idea of Sec. II.C generalised to radix R in
+// {2, 3, 4, 5, 8, 16} (a Stockham auto-sort decimation-in-time ordering, so
+// no bit reversal pass is needed).  Each thread holds E elements in registers;
+// thread t of a segment owns indices t + Tseg*s (s < E, Tseg = L/E) both on
+// entry and on exit, so global loads and stores are coalesced and a forward
+// transform can hand its output straight to an inverse one in registers.
+// Stages exchange data through shared memory.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fs_desc.h"
+
+namespace fs {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T x, T y) {
+  cx<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk<T>(s * a.x, s * a.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> conj(cx<T> a) { return mk<T>(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse): the quarter-turn of omega_4
+template <bool INV, typename T>
+__device__ __forceinline__ cx<T> rot4(cx<T> a) {
+  return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+// multiply by a constant root of unity given as (cos, sin) of the forward angle:
+// forward uses cos - i sin, inverse cos + i sin.
+template <bool INV, typename T>
+__device__ __forceinline__ cx<T> crot(cx<T> a, T c, T s) {
+  const T si = INV ? s : -s;
+  return mk<T>(a.x * c - a.y * si, a.x * si + a.y * c);
+}
+
+// Mathematical constants (cos/sin of rational multiples of pi), 20 digits.
+#define FS_SQRT1_2 0.70710678118654752440
+#define FS_COS_PI8 0.92387953251128675613
+#define FS_SIN_PI8 0.38268343236508977173
+#define FS_SIN_PI3 0.86602540378443864676
+#define FS_COS_2PI5 0.30901699437494742410
+#define FS_SIN_2PI5 0.95105651629515357212
+#define FS_COS_4PI5 (-0.80901699437494742410)
+#define FS_SIN_4PI5 0.58778525229247312917
+
+// ------------------------------------------------------------ butterflies
+// In-place R-point DFT of b[0..R-1]: X_k = sum_n b_n w^{nk}, w = e^{-+2 pi i/R}.
+template <bool INV, typename T>
+__device__ __forceinline__ void dft2(cx<T> *b) {
+  cx<T> a0 = b[0], a1 = b[1];
+  b[0] = a0 + a1;
+  b[1] = a0 - a1;
+}
+
+template <bool INV, typename T>
+__device__ __forceinline__ void dft3(cx<T> *b) {
+  const T h = T(FS_SIN_PI3);
+  cx<T> t = b[1] + b[2];
+  cx<T> d = b[1] - b[2];
+  cx<T> m = b[0] - T(0.5) * t;
+  // (-+ i sqrt(3)/2) d
+  cx<T> r = INV ? mk<T>(-h * d.y, h * d.x) : mk<T>(h * d.y, -h * d.x);
+  b[0] = b[0] + t;
+  b[1] = m + r;
+  b[2] = m - r;
+}
+
+template <bool INV, typename T>
+__device__ __forceinline__ void dft4(cx<T> *b) {
+  cx<T> t0 = b[0] + b[2], t1 = b[0] - b[2];
+  cx<T> t2 = b[1] + b[3], t3 = rot4<INV>(b[1] - b[3]);
+  b[0] = t0 + t2;
+  b[2] = t0 - t2;
+  b[1] = t1 + t3;
+  b[3] = t1 - t3;
+}
+
+template <bool INV, typename T>
+__device__ __forceinline__ void dft5(cx<T> *b) {
+  const T c1 = T(FS_COS_2PI5), s1 = T(FS_SIN_2PI5);
+  const T c2 = T(FS_COS_4PI5), s2 = T(FS_SIN_4PI5);
+  cx<T> t1 = b[1] + b[4], d1 = b[1] - b[4];
+  cx<T> t2 = b[2] + b[3], d2 = b[2] - b[3];
+  cx<T> a0 = b[0];
+  cx<T> r1 = a0 + c1 * t1 + c2 * t2;
+  cx<T> r2 = a0 + c2 * t1 + c1 * t2;
+  cx<T> q1 = s1 * d1 + s2 * d2;  // multiplies -+ i
+  cx<T> q2 = s2 * d1 - s1 * d2;
+  cx<T> i1 = rot4<INV>(q1);
+  cx<T> i2 = rot4<INV>(q2);
+  b[0] = a0 + t1 + t2;
+  b[1] = r1 + i1;
+  b[4] = r1 - i1;
+  b[2] = r2 + i2;
+  b[3] = r2 - i2;
+}
+
+template <bool INV, typename T>
+__device__ __forceinline__ void dft8(cx<T> *b) {
+  cx<T> e[4] = {b[0], b[2], b[4], b[6]};
+  cx<T> o[4] = {b[1], b[3], b[5], b[7]};
+  dft4<INV>(e);
+  dft4<INV>(o);
+  const T r = T(FS_SQRT1_2);
+  cx<T> w1 = crot<INV>(o[1], r, r);
+  cx<T> w2 = rot4<INV>(o[2]);
+  cx<T> w3 = crot<INV>(o[3], -r, r);
+  b[0] = e[0] + o[0];
+  b[4] = e[0] - o[0];
+  b[1] = e[1] + w1;
+  b[5] = e[1] - w1;
+  b[2] = e[2] + w2;
+  b[6] = e[2] - w2;
+  b[3] = e[3] + w3;
+  b[7] = e[3] - w3;
+}
+
+template <bool INV, typename T>
+__device__ __forceinline__ void dft16(cx<T> *b) {
+  cx<T> e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    e[i] = b[2 * i];
+    o[i] = b[2 * i + 1];
+  }
+  dft8<INV>(e);
+  dft8<INV>(o);
+  const T c1 = T(FS_COS_PI8), s1 = T(FS_SIN_PI8), r = T(FS_SQRT1_2);
+  cx<T> w[8];
+  w[0] = o[0];
+  w[1] = crot<INV>(o[1], c1, s1);
+  w[2] = crot<INV>(o[2], r, r);
+  w[3] = crot<INV>(o[3], s1, c1);
+  w[4] = rot4<INV>(o[4]);
+  w[5] = crot<INV>(o[5], -s1, c1);
+  w[6] = crot<INV>(o[6], -r, r);
+  w[7] = crot<INV>(o[7], -c1, s1);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    b[i] = e[i] + w[i];
+    b[i + 8] = e[i] - w[i];
+  }
+}
+
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void dftR(cx<T> *b) {
+  if constexpr (R == 2) dft2<INV>(b);
+  else if constexpr (R == 3) dft3<INV>(b);
+  else if constexpr (R == 4) dft4<INV>(b);
+  else if constexpr (R == 5) dft5<INV>(b);
+  else if constexpr (R == 8) dft8<INV>(b);
+  else if constexpr (R == 16) dft16<INV>(b);
+}
+
+// ------------------------------------------------------------ shared exchange
+// Element idx of a segment lives at smem word pad(base + idx*sidx); one pad
+// slot per 16 elements breaks the power-of-two strides of the early stages.
+struct XLayout {
+  int base;
+  int sidx;
+};
+__device__ __forceinline__ int padi(int p) { return p + (p >> 4); }
+__host__ __device__ inline int padded_len(int n) { return n + (n >> 4) + 1; }
+
+// One Stockham stage of radix R on the register tile.  Butterfly j = t + q*Tseg
+// reads (already in registers, canonical slots q + r*E/R) elements j + r*L/R,
+// applies the twiddles w_{Ns R}^{(j mod Ns) r}, and produces outputs that
+// belong at indices expand(j) + r*Ns, expand(j) = (j/Ns)*Ns*R + j mod Ns.
+template <typename T, int E, int R>
+__device__ __forceinline__ void stage_compute(cx<T> (&v)[E], int t, int Tseg, int L, int Ns,
+                                              const cx<T> *__restrict__ tw, int twmul) {
+  if constexpr (E % R != 0) {
+    return;
+  } else {
+    constexpr int Q = E / R;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int j = t + q * Tseg;
+      cx<T> b[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) b[r] = v[q + r * Q];
+      if (Ns > 1) {
+        const int k = j % Ns;
+        const int step = twmul * k * (L / (Ns * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) b[r] = cmul(b[r], tw[step * r]);
+      }
+      dftR<R, false>(b);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q + r * Q] = b[r];
+    }
+  }
+}
+
+template <typename T, int E, int R>
+__device__ __forceinline__ void stage_store(const cx<T> (&v)[E], cx<T> *sm, XLayout lay, int t,
+                                            int Tseg, int Ns) {
+  if constexpr (E % R != 0) {
+    return;
+  } else {
+    constexpr int Q = E / R;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int j = t + q * Tseg;
+      const int k = j % Ns;
+      const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[padi(lay.base + (base + r * Ns) * lay.sidx)] = v[q + r * Q];
+    }
+  }
+}
+
+// Full forward transform (e^{-2 pi i} kernel).  Every thread of the block must
+// call it (it synchronises); inactive threads carry no data.  On return the
+// register tile holds the result in canonical order; the caller must
+// __syncthreads() before it next writes `sm` (other threads may still read the
+// last exchange).  The inverse transform is obtained from the forward one by
+// conjugating input and output (the iDFT identity stated after Eq. DFT2).
+template <typename T, int E>
+__device__ __forceinline__ void fft_run(cx<T> (&v)[E], cx<T> *sm, XLayout lay, bool active, int t, int Tseg,
+                        int L, const RadixPlan &rp, const cx<T> *__restrict__ tw, int twmul) {
+  int Ns = 1;
+  const int n = rp.n;
+  for (int st = 0; st < n; ++st) {
+    const int R = rp.r[st];
+    if (st > 0 && active) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) v[s] = sm[padi(lay.base + (t + Tseg * s) * lay.sidx)];
+    }
+    if (active) {
+      switch (R) {
+        case 2: stage_compute<T, E, 2>(v, t, Tseg, L, Ns, tw, twmul); break;
+        case 3: stage_compute<T, E, 3>(v, t, Tseg, L, Ns, tw, twmul); break;
+        case 4: stage_compute<T, E, 4>(v, t, Tseg, L, Ns, tw, twmul); break;
+        case 5: stage_compute<T, E, 5>(v, t, Tseg, L, Ns, tw, twmul); break;
+        case 8: stage_compute<T, E, 8>(v, t, Tseg, L, Ns, tw, twmul); break;
+        case 16: stage_compute<T, E, 16>(v, t, Tseg, L, Ns, tw, twmul); break;
+        default: break;
+      }
+    }
+    if (st < n - 1) {
+      __syncthreads();
+      if (active) {
+        switch (R) {
+          case 2: stage_store<T, E, 2>(v, sm, lay, t, Tseg, Ns); break;
+          case 3: stage_store<T, E, 3>(v, sm, lay, t, Tseg, Ns); break;
+          case 4: stage_store<T, E, 4>(v, sm, lay, t, Tseg, Ns); break;
+          case 5: stage_store<T, E, 5>(v, sm, lay, t, Tseg, Ns); break;
+          case 8: stage_store<T, E, 8>(v, sm, lay, t, Tseg, Ns); break;
+          case 16: stage_store<T, E, 16>(v, sm, lay, t, Tseg, Ns); break;
+          default: break;
+        }
+      }
+      __syncthreads();
+    }
+    Ns *= R;
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void conj_tile(cx<T> (&v)[E]) {
+#pragma unroll
+  for (int s = 0; s < E; ++s) v[s].y = -v[s].y;
+}
+template <typename T, int E>
+__device__ __forceinline__ void swap_tile(cx<T> (&a)[E], cx<T> (&b)[E]) {
+#pragma unroll
+  for (int s = 0; s < E; ++s) {
+    const cx<T> t = a[s];
+    a[s] = b[s];
+    b[s] = t;
+  }
+}
+
+}  // namespace fs

@@ -1,0 +1,60 @@
+// fs_host.h -- host-side plan/state objects shared by the C-ABI sources.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include "../../include/fsolve.h"
+#include "fs_desc.h"
+
+namespace fs {
+
+extern std::atomic<unsigned long long> g_launches;
+
+fs_status set_error(fs_status st, const std::string &msg);
+fs_status cuda_error(cudaError_t e, const char *what);
+
+// Radix factorisation and register-tile choice for a length-L transform.
+int choose_e(int L, bool f64);
+int radix_plan(int L, int e, int *out, int cap);
+bool size_supported(int n);
+
+struct TileConfig {
+  int rows_per_unit;  // row passes
+  int cols_per_unit;  // column pass
+  int small_rows, small_cols;
+  size_t small_smem1, small_smem2;  // small-path smem with one / two resident spectra (0: too big)
+};
+
+}  // namespace fs
+
+struct fs_plan_s {
+  int nx, ny, M, dtype;
+  double lx, ly;
+  int device;
+  fs::RadixPlan rp_row, rp_col;
+  fs::TileConfig tc;
+  bool standalone_small;  // single-kernel path for one-off calls
+  size_t csize;           // bytes per complex element
+  // device tables (one allocation)
+  void *tables;
+  void *tw_x, *tw_y, *wx2, *wy2;
+  double *wx2d, *wy2d;
+  // device workspace
+  void *work_u, *work_v, *fac;
+  size_t spec_bytes;  // (M+1)*ny complex
+};
+
+struct fs_state_s {
+  fs_plan plan;
+  void *su, *sv;
+  bool has_v;
+};
+
+namespace fs {
+// Descriptor with the plan's geometry, tables and tile shapes filled in.
+Desc base_desc(const fs_plan_s *p);
+size_t fac_bytes(const fs_plan_s *p);
+}  // namespace fs

@@ -1,0 +1,230 @@
+// fs_kernels.cuh -- __global__ entry points built from the units, and their
+// host-side launchers.  Included once per element type (fs_kernels_f32.cu,
+// fs_kernels_f64.cu) so the two precisions compile in parallel.
+#pragma once
+#include <atomic>
+
+#include "fs_units.cuh"
+
+namespace fs {
+
+extern std::atomic<unsigned long long> g_launches;
+
+constexpr int kMaxThreads = 512;
+constexpr int kFactorPerUnit = 256;  // factor-table entries per factor unit
+
+// ---------------------------------------------------------------- pass kernels
+// The row R2C / column / row C2R pass kernels are defined per register tile in
+// fs_units_inst.cu (k_r2c_<T>_<E>, k_col1/k_col2_<T>_<E>, k_c2r_<T>_<E>) so
+// that each inlines its unit; the launchers below select them by tile size.
+
+// Diffusion per-axis factor tables: grid = n_fac_units, 256 threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_factor(const Desc d) {
+  unit_factor<T>(d, blockIdx.x * kFactorPerUnit, kFactorPerUnit, 256);
+}
+
+// Small grids: the whole solve in one CTA, grid = 1.
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_small(const Desc d) {
+  extern __shared__ __align__(16) unsigned char fs_smem[];
+  unit_small<T>(d, reinterpret_cast<cx<T> *>(fs_smem));
+}
+
+// ---------------------------------------------------------------- persistent batch
+// Work unit: x = problem, y = kind (K_*), z = unit index within its kind,
+// w = field (0: u, 1: v).  Units are listed so that every dependency of a
+// unit has a smaller index; CTAs take indices from ctl[0] in order, so a unit
+// only ever waits on units already taken by running CTAs.
+//   ctl[0] next unit, ctl[1] status (0 ok, else an fs_status),
+//   done[5*p + kind] units of that kind finished for problem p.
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_batch(const Desc *__restrict__ descs,
+                                                       const int4 *__restrict__ units, int n_units,
+                                                       int *ctl, int *done,
+                                                       unsigned long long wait_ns) {
+  extern __shared__ __align__(16) unsigned char fs_smem[];
+  __shared__ Desc sd;
+  __shared__ int s_unit, s_abort;
+  cx<T> *sm = reinterpret_cast<cx<T> *>(fs_smem);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_unit = atomicAdd(&ctl[0], 1);
+      s_abort = 0;
+    }
+    __syncthreads();
+    const int k = s_unit;
+    if (k >= n_units) break;
+    const int4 u = units[k];
+    // copy the descriptor into shared memory (word by word)
+    {
+      const int *src = reinterpret_cast<const int *>(descs + u.x);
+      int *dst = reinterpret_cast<int *>(&sd);
+      for (int i = threadIdx.x; i < (int)(sizeof(Desc) / sizeof(int)); i += blockDim.x)
+        dst[i] = src[i];
+    }
+    if (threadIdx.x == 0) {
+      // dependencies: columns need every row tile (and factor range) of the
+      // problem, the C2R tiles need every column group.
+      const Desc &dd = descs[u.x];
+      int need0 = -1, cnt0 = 0, need1 = -1, cnt1 = 0;
+      if (u.y == K_COL) {
+        const bool adv = (dd.op == OP_DIFF_ADV || dd.op == OP_WAVE_ADV);
+        const bool two = (dd.op == OP_WAVE || dd.op == OP_FORWARD) && (dd.flags & F_HAS_V0);
+        if (!adv) {
+          need0 = K_ROW;
+          cnt0 = dd.n_row_units * (two ? 2 : 1);
+        }
+        if (dd.op == OP_DIFFUSION || dd.op == OP_DIFF_ADV) {
+          need1 = K_FACTOR;
+          cnt1 = dd.n_fac_units;
+        }
+      } else if (u.y == K_C2R) {
+        need0 = K_COL;
+        cnt0 = dd.n_col_units;
+      }
+      const unsigned long long t0 = global_ns();
+      for (int pass = 0; pass < 2 && !s_abort; ++pass) {
+        const int need = pass ? need1 : need0, cnt = pass ? cnt1 : cnt0;
+        if (need < 0) continue;
+        unsigned ns = 32;
+        while (ld_acquire(&done[5 * u.x + need]) < cnt) {
+          if (ld_acquire(&ctl[1]) != 0) {
+            s_abort = 1;
+            break;
+          }
+          if (global_ns() - t0 > wait_ns) {
+            atomicCAS(&ctl[1], 0, -6 /* FS_ERR_TIMEOUT */);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(ns);
+          if (ns < 1024) ns <<= 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    const Desc &d = sd;
+    switch (u.y) {
+      case K_FACTOR:
+        unit_factor<T>(d, u.z * kFactorPerUnit, kFactorPerUnit, blockDim.x);
+        break;
+      case K_ROW:
+        row_r2c_any<T>(d, u.z, d.rows_per_unit, sm,
+                              reinterpret_cast<const T *>(u.w ? d.in_v : d.in_u),
+                              reinterpret_cast<cx<T> *>(u.w ? d.work_v : d.work_u));
+        break;
+      case K_SMALL:
+        unit_small<T>(d, sm);
+        break;
+      case K_COL:
+        col_any<T>(d, u.z, d.cols_per_unit, sm, reinterpret_cast<cx<T> *>(d.work_u),
+                   reinterpret_cast<cx<T> *>(d.work_v), false);
+        break;
+      case K_C2R:
+        row_c2r_any<T>(d, u.z, d.rows_per_unit, sm,
+                       reinterpret_cast<const cx<T> *>(u.w ? d.work_v : d.work_u),
+                       reinterpret_cast<T *>(u.w ? d.out_v : d.out_u), false);
+        break;
+      default:
+        break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&done[5 * u.x + u.y], 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+inline int round_up32(int n) { return (n + 31) / 32 * 32; }
+
+template <typename T>
+struct Launch {
+  static size_t row_smem(const Desc &d) {
+    return sizeof(cx<T>) * (size_t)padded_len(d.rows_per_unit * d.M);
+  }
+  static size_t col_smem(const Desc &d) {
+    return sizeof(cx<T>) * (size_t)padded_len(d.cols_per_unit * d.ny);
+  }
+  static int row_threads(const Desc &d) { return round_up32(d.rows_per_unit * (d.M / d.rp_row.e)); }
+  static int col_threads(const Desc &d) { return round_up32(d.cols_per_unit * (d.ny / d.rp_col.e)); }
+  static size_t small_smem(const Desc &d) {
+    const size_t spec = (size_t)(d.M + 1) * d.ny * small_nspec(d);
+    const size_t x1 = padded_len(d.small_rows * d.M), x2 = padded_len(d.small_cols * d.ny);
+    return sizeof(cx<T>) * (spec + (x1 > x2 ? x1 : x2));
+  }
+  static int small_threads(const Desc &d) {
+    const int a = d.small_rows * (d.M / d.rp_row.e), b = d.small_cols * (d.ny / d.rp_col.e);
+    return round_up32(a > b ? a : b);
+  }
+  static cudaError_t set_smem(const void *fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
+
+  static cudaError_t launch(PassKernel k, int grid, int threads, size_t sm, const Desc &d,
+                            cudaStream_t s) {
+    if (!k) return cudaErrorInvalidConfiguration;
+    cudaError_t e = set_smem((const void *)k, sm);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads, sm, s>>>(d);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+  }
+  // forward pass over the real field(s): fields = 1 or 2
+  static cudaError_t rows(const Desc &d, int fields, cudaStream_t s) {
+    return launch(pass_kernels<T>(d.rp_row.e).r2c, d.n_row_units * fields, row_threads(d),
+                  row_smem(d), d, s);
+  }
+  static cudaError_t cols(const Desc &d, cudaStream_t s) {
+    const PassKernels pk = pass_kernels<T>(d.rp_col.e);
+    return launch(col_two_fields(d) ? pk.col2 : pk.col1, d.n_col_units, col_threads(d),
+                  col_smem(d), d, s);
+  }
+  static cudaError_t c2r(const Desc &d, int fields, cudaStream_t s) {
+    return launch(pass_kernels<T>(d.rp_row.e).c2r, d.n_row_units * fields, row_threads(d),
+                  row_smem(d), d, s);
+  }
+  static cudaError_t factor(const Desc &d, cudaStream_t s) {
+    k_factor<T><<<d.n_fac_units, 256, 0, s>>>(d);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+  }
+  static cudaError_t small(const Desc &d, cudaStream_t s) {
+    const size_t sm = small_smem(d);
+    cudaError_t e = set_smem((const void *)k_small<T>, sm);
+    if (e != cudaSuccess) return e;
+    k_small<T><<<1, small_threads(d), sm, s>>>(d);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+  }
+  static cudaError_t batch(const Desc *descs, const int4 *units, int n_units, int *ctl, int *done,
+                           int grid, size_t smem, unsigned long long wait_ns, cudaStream_t s) {
+    cudaError_t e = set_smem((const void *)k_batch<T>, smem);
+    if (e != cudaSuccess) return e;
+    k_batch<T><<<grid, kMaxThreads, smem, s>>>(descs, units, n_units, ctl, done, wait_ns);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+  }
+  static cudaError_t batch_occupancy(size_t smem, int *per_sm) {
+    cudaError_t e = set_smem((const void *)k_batch<T>, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<T>, kMaxThreads, smem);
+  }
+};
+
+}  // namespace fs

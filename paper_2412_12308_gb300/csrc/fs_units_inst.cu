@@ -1,0 +1,17 @@
+// Instantiates the work units for one element type and register tile size.
+// Compiled once per (FS_T, FS_E) pair by the build, as relocatable device code.
+#include "fs_units.cuh"
+
+#ifndef FS_T
+#error "FS_T (float or double) must be defined"
+#endif
+#ifndef FS_E
+#error "FS_E (register tile size) must be defined"
+#endif
+
+// expand FS_T / FS_E before token pasting
+#define FS_UNIT_DEF_X(T, E) FS_UNIT_DEF(T, E)
+
+namespace fs {
+FS_UNIT_DEF_X(FS_T, FS_E)
+}

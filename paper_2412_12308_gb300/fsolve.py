@@ -1,0 +1,195 @@
+"""ctypes binding of the C ABI in include/fsolve.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does
+nothing but convert arguments: torch tensors become device pointers
+(``data_ptr()``), a torch stream (or None = the current stream) becomes a
+``cudaStream_t``, and a non-zero ``fs_status`` becomes an ``FsError`` carrying
+``fs_last_error()``.  All computation happens in ``libfsolve.so``.  There is no
+fallback: if the library is missing, ``load()`` raises.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfsolve.so")
+
+FS_F32 = 0
+FS_F64 = 1
+
+FS_OK = 0
+STATUS_NAMES = {
+    0: "FS_OK", -1: "FS_ERR_ARG", -2: "FS_ERR_SIZE", -3: "FS_ERR_NOMEM", -4: "FS_ERR_BUDGET",
+    -5: "FS_ERR_CUDA", -6: "FS_ERR_TIMEOUT", -7: "FS_ERR_BUSY", -8: "FS_ERR_NODEV",
+}
+
+FS_OP_POISSON = 0
+FS_OP_DIFFUSION = 1
+FS_OP_WAVE = 2
+FS_OP_DIFFUSION_ADVANCE = 3
+FS_OP_WAVE_ADVANCE = 4
+
+# Entry points declared in include/fsolve.h: name -> (restype, argtypes)
+_vp = ctypes.c_void_p
+_SIGS = {
+    "fs_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, ctypes.POINTER(_vp)]),
+    "fs_plan_destroy": (ctypes.c_int, [_vp]),
+    "fs_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_size_t)]),
+    "fs_poisson_solve": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "fs_diffusion_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "fs_wave_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "fs_state_create": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "fs_state_destroy": (ctypes.c_int, [_vp]),
+    "fs_diffusion_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "fs_wave_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
+    "fs_last_error": (ctypes.c_char_p, []),
+    "fs_size_supported": (ctypes.c_int, [ctypes.c_int]),
+    "fs_radix_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "fs_kernel_launches": (ctypes.c_uint64, []),
+}
+
+_lib = None
+
+
+class FsError(RuntimeError):
+    def __init__(self, status, where, message):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+def load(path=None):
+    """Load libfsolve.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C entry points this binding marshals."""
+    return sorted(_SIGS)
+
+
+def _check(status, where):
+    if status != FS_OK:
+        msg = _lib.fs_last_error()
+        raise FsError(status, where, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        import torch
+
+        s = torch.cuda.current_stream()
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------ entry points
+def fs_plan_create(nx, ny, lx, ly, dtype):
+    load()
+    h = _vp()
+    _check(_lib.fs_plan_create(int(nx), int(ny), float(lx), float(ly), int(dtype), ctypes.byref(h)),
+           "fs_plan_create")
+    return h
+
+
+def fs_plan_destroy(plan):
+    load()
+    _check(_lib.fs_plan_destroy(plan), "fs_plan_destroy")
+
+
+def fs_plan_info(plan):
+    load()
+    nx, ny, dt, path = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ws = ctypes.c_size_t()
+    _check(_lib.fs_plan_info(plan, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(dt),
+                             ctypes.byref(path), ctypes.byref(ws)), "fs_plan_info")
+    return {"nx": nx.value, "ny": ny.value, "dtype": dt.value, "path": path.value,
+            "workspace_bytes": ws.value}
+
+
+def fs_poisson_solve(plan, f, u, stream=None):
+    load()
+    _check(_lib.fs_poisson_solve(plan, _ptr(f), _ptr(u), _stream(stream)), "fs_poisson_solve")
+
+
+def fs_diffusion_solve(plan, u0, D, t, u, stream=None):
+    load()
+    _check(_lib.fs_diffusion_solve(plan, _ptr(u0), float(D), float(t), _ptr(u), _stream(stream)),
+           "fs_diffusion_solve")
+
+
+def fs_wave_solve(plan, u0, v0, c, t, u, stream=None):
+    load()
+    _check(_lib.fs_wave_solve(plan, _ptr(u0), _ptr(v0), float(c), float(t), _ptr(u), _stream(stream)),
+           "fs_wave_solve")
+
+
+def fs_state_create(plan, u0, v0=None, stream=None):
+    load()
+    h = _vp()
+    _check(_lib.fs_state_create(plan, _ptr(u0), _ptr(v0), _stream(stream), ctypes.byref(h)),
+           "fs_state_create")
+    return h
+
+
+def fs_state_destroy(state):
+    load()
+    _check(_lib.fs_state_destroy(state), "fs_state_destroy")
+
+
+def fs_diffusion_advance(state, D, t, u_out, stream=None):
+    load()
+    _check(_lib.fs_diffusion_advance(state, float(D), float(t), _ptr(u_out), _stream(stream)),
+           "fs_diffusion_advance")
+
+
+def fs_wave_advance(state, c, t, u_out, v_out=None, stream=None):
+    load()
+    _check(_lib.fs_wave_advance(state, float(c), float(t), _ptr(u_out), _ptr(v_out), _stream(stream)),
+           "fs_wave_advance")
+
+
+def fs_last_error():
+    load()
+    m = _lib.fs_last_error()
+    return m.decode() if m else ""
+
+
+def fs_size_supported(n):
+    load()
+    return bool(_lib.fs_size_supported(int(n)))
+
+
+def fs_radix_plan(L, e):
+    load()
+    buf = (ctypes.c_int * 8)()
+    n = _lib.fs_radix_plan(int(L), int(e), buf, 8)
+    return [buf[i] for i in range(n)]
+
+
+def fs_kernel_launches():
+    load()
+    return int(_lib.fs_kernel_launches())

@@ -1,0 +1,109 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library must load, export every entry point that include/fsolve.h
+declares, and reject bad arguments before touching a device.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2412_12308_gb300 import fsolve, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fsolve.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(fs_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(fsolve.LIB_PATH):
+        import __graft_entry__
+
+        __graft_entry__.build()
+    return fsolve.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("fs_plan_create", "fs_poisson_solve", "fs_diffusion_advance", "fs_wave_advance",
+                 "fs_state_create", "fs_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, f"declared in include/fsolve.h but not exported: {missing}"
+
+
+def test_binding_names_match_header():
+    declared = set(_declared())
+    for name in fsolve.exported_symbols():
+        assert name in declared, name
+
+
+def test_size_rule_matches_generator(lib):
+    for n in range(0, 8200, 2):
+        assert fsolve.fs_size_supported(n) == workloads.is_supported_size(n), n
+    for n in (7, 9, 14, 28, 56, 8194, 16384, -8):
+        assert not fsolve.fs_size_supported(n)
+
+
+@pytest.mark.parametrize("L,e", [(4, 4), (8, 8), (16, 16), (32, 16), (2048, 16), (4096, 16), (8192, 16),
+                                 (6, 6), (12, 12), (24, 24), (48, 24), (3072, 24), (6144, 24),
+                                 (5, 5), (10, 10), (20, 20), (40, 20), (5120, 20), (8192, 8)])
+def test_radix_plan_product_and_divisibility(lib, L, e):
+    r = fsolve.fs_radix_plan(L, e)
+    assert r, (L, e)
+    prod = 1
+    for x in r:
+        assert x in (2, 3, 4, 5, 8, 16)
+        assert e % x == 0, (L, e, r)
+        prod *= x
+    assert prod == L
+
+
+def test_radix_plan_rejects_bad_lengths(lib):
+    assert fsolve.fs_radix_plan(7, 8) == []
+    assert fsolve.fs_radix_plan(24, 16) == []  # odd factor 3 does not divide the tile
+    assert fsolve.fs_radix_plan(0, 16) == []
+
+
+@pytest.mark.parametrize("nx,ny", [(7, 8), (8, 14), (8194, 8), (6, 8), (8, 0), (9, 9)])
+def test_plan_create_rejects_sizes_without_device(lib, nx, ny):
+    h = ctypes.c_void_p()
+    st = lib.fs_plan_create(nx, ny, 1.0, 1.0, 0, ctypes.byref(h))
+    assert st == -2  # FS_ERR_SIZE, decided on the host before any CUDA call
+    assert not h.value
+    assert b"unsupported size" in lib.fs_last_error()
+
+
+def test_plan_create_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.fs_plan_create(64, 64, 0.0, 1.0, 0, ctypes.byref(h)) == -1
+    assert lib.fs_plan_create(64, 64, 1.0, -1.0, 0, ctypes.byref(h)) == -1
+    assert lib.fs_plan_create(64, 64, 1.0, 1.0, 7, ctypes.byref(h)) == -1
+    assert lib.fs_plan_create(64, 64, 1.0, 1.0, 0, None) == -1
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.fs_poisson_solve(None, None, None, None) == -1
+    assert lib.fs_diffusion_advance(None, 0.1, 0.0, None, None) == -1
+    assert lib.fs_wave_advance(None, 1.0, 0.0, None, None, None) == -1
+    assert lib.fs_plan_destroy(None) == 0
+    assert lib.fs_state_destroy(None) == 0
+
+
+def test_binding_raises_with_message(lib):
+    with pytest.raises(fsolve.FsError) as ei:
+        fsolve.fs_plan_create(10, 7, 1.0, 1.0, fsolve.FS_F32)
+    assert ei.value.status == -2
+    assert "unsupported size" in str(ei.value)
