@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the 2D Fourier-space solve on GB300 (one JSON line on stdout).
+
+Default workload (one "step"): diffusion u_t = D lap u on periodic
+[0, 2 pi)^2, 1024 x 1024, FP32, D = 0.1, initial field = 16 seeded periodic
+Gaussian blobs; the spectrum is computed once per step and kept on the
+device, then u(t) is produced at 100 output times evenly spaced in [0, 1].
+A step = 1 forward transform into the kept state + 100 advances (inverse
+transforms), i.e. 100 solves.  The metric is solves per second.
+
+Arms:
+  --impl ours        this library through its C ABI (default)
+  --impl reference   the float64 CPU oracle on the host cores (bounded sample
+                     of the same workload per step, scaled to the step)
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own copy of the
+workload (replicas, weak scaling); the time is the max over ranks.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D solves/s & HBM GB/s vs plain GPU path at rel-L2≤1e-5; served p50/p99 latency"
+N = 1024
+N_TIMES = 100
+WORKLOAD = ("diffusion u_t = D lap u, periodic [0,2pi)^2, 1024x1024 FP32, D=0.1, 16 seeded "
+            "Gaussian blobs, spectrum kept on device, 100 output times evenly spaced in [0,1]")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = False
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend)
+            self.pg = True
+
+    def barrier(self):
+        if self.pg:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="fs_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            out["reasons"] = ["nvidia-smi unavailable"]
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows]
+        out["samples"] = len(rows)
+        out["sm_mhz"] = statistics.median(sm)
+        out["sm_max_mhz"] = float(rows[0][2])
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        out["reasons"] = sorted(reasons)
+        out["power_w_max"] = max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+        return out
+
+
+# ----------------------------------------------------------------------------- workload
+def workload():
+    from paper_2412_12308_gb300 import workloads
+
+    u0, blobs, (lx, ly), D, times = workloads.diffusion_blobs_1024(n=N, n_times=N_TIMES)
+    return u0.astype(np.float32), blobs, lx, ly, D, times
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=5):
+    """The float64 oracle as it stands, on a bounded sample of the workload:
+    one forward 2D DFT (the kept spectrum) and n_snap of the output times,
+    scaled to a full step (1 forward + 100 outputs)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    F = oracle.state_spectrum(u0.astype(np.float64))
+    t_fwd = time.perf_counter() - t0
+    pick = np.linspace(0, len(times) - 1, n_snap).round().astype(int)
+    t1 = time.perf_counter()
+    outs = []
+    for j in pick:
+        U = oracle.diffusion_spectrum(F, D, float(times[j]), lx, ly)
+        outs.append(np.real(oracle.idft2(U)))
+    t_snap = (time.perf_counter() - t1) / len(pick)
+    step_s = t_fwd + len(times) * t_snap
+    res = {
+        "value": len(times) / step_s,
+        "unit": "solves/s",
+        "cores": os.cpu_count(),
+        "kind": "oracle",
+        "sample": f"float64 direct-DFT oracle: 1 forward 2D DFT + {len(pick)} of the {len(times)} output "
+                  f"times (t = {', '.join(f'{float(times[j]):.3f}' for j in pick)}), scaled to 1 forward + "
+                  f"{len(times)} outputs",
+        "seconds": t_fwd + t_snap * len(pick),
+    }
+    if gpu_out is not None:
+        errs = []
+        for k, j in enumerate(pick):
+            g = gpu_out[j].astype(np.float64)
+            errs.append(float(np.linalg.norm(g - outs[k]) / np.linalg.norm(outs[k])))
+        res["rel_l2_vs_oracle_max"] = max(errs)
+    return res
+
+
+# ----------------------------------------------------------------------------- ours
+def run_ours(args, dist):
+    import torch
+
+    from paper_2412_12308_gb300 import fsolve
+
+    torch.cuda.set_device(dist.local)
+    dist.init("nccl")
+    fsolve.load()
+    u0, blobs, lx, ly, D, times = workload()
+    dev = torch.device("cuda", dist.local)
+    plan = fsolve.fs_plan_create(N, N, lx, ly, fsolve.FS_F32)
+    u0d = torch.tensor(u0, device=dev)
+    out = torch.empty((len(times), N, N), dtype=torch.float32, device=dev)
+    state = fsolve.fs_state_create(plan, u0d)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    ts = [float(t) for t in times]
+
+    def step(src):
+        fsolve.fs_state_reset(state, src)
+        for j, t in enumerate(ts):
+            fsolve.fs_diffusion_advance(state, D, t, out[j])
+
+    for _ in range(args.warmup):
+        step(u0d)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps (untimed)
+    clocks = Clocks(dist.local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = fsolve.fs_kernel_launches()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        step(u0d)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    launches = (fsolve.fs_kernel_launches() - l0) // max(1, args.steps)
+    clk = clocks.stop()
+    dist.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    total_ms = dist.max(total_ms)
+    ms_per_step = total_ms / args.steps
+    value = dist.world * len(ts) * args.steps / (total_ms / 1e3)
+
+    # ---- per-kernel device time (library events on the launching stream), same steps
+    fsolve.fs_profile_enable(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step(u0d)
+    torch.cuda.synchronize()
+    prof = fsolve.fs_profile_report()
+    fsolve.fs_profile_enable(False)
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (cnt, tot) = dom
+    avg_s = tot / max(1, cnt) / 1e3
+    M = N // 2
+    spec_bytes = (M + 1) * N * 8
+    # algorithmic bytes per launch (FP32): column advance reads the kept
+    # spectrum and writes the work spectrum; C2R reads the work spectrum and
+    # writes the real field; R2C reads the field and writes the spectrum.
+    algo = {"column": 2 * spec_bytes, "row_c2r": spec_bytes + N * N * 4, "row_r2c": N * N * 4 + spec_bytes,
+            "factor": (M + 1 + N) * 16}.get(name, 0)
+    peak, peak_src = peaks()
+    achieved = algo / avg_s / 1e9 if avg_s > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": name,
+                "peak_source": peak_src, "avg_launch_us": round(avg_s * 1e6, 3),
+                "algorithmic_bytes_per_launch": algo,
+                "per_kernel_ms": {k: round(v[1] / max(1, v[0]), 5) for k, v in prof.items() if v[0]}}
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    h_u0 = torch.from_numpy(u0).pin_memory()
+    h_out = torch.empty((len(ts), N, N), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        u0d.copy_(h_u0, non_blocking=True)
+        step(u0d)
+        h_out.copy_(out, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_step = dist.max(statistics.median(e2e_ms))
+    e2e = {"value": dist.world * len(ts) / (e2e_step / 1e3), "unit": "solves/s",
+           "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(len(ts) * N * N * 4)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "solves/s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Gaussian blobs)",
+        "config": {"workload": WORKLOAD, "grid": [N, N], "solves_per_step": len(ts),
+                   "l2": "flushed between steps (256 MB write, untimed)",
+                   "parallelism": f"replicas x{dist.world}"},
+        "e2e": e2e, "roofline": roofline, "gpu_launches": int(launches), "clocks": clk,
+    }
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        gpu_out = out.cpu().numpy()
+        line["cpu_baseline"] = cpu_baseline(u0, lx, ly, D, times, gpu_out)
+        line["rel_l2_vs_oracle_max"] = line["cpu_baseline"].pop("rel_l2_vs_oracle_max", None)
+    fsolve.fs_state_destroy(state)
+    fsolve.fs_plan_destroy(plan)
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+# ----------------------------------------------------------------------------- reference
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    u0, blobs, lx, ly, D, times = workload()
+    samples = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(u0, lx, ly, D, times, None, n_snap=3)
+        if k >= args.warmup:
+            samples.append(r)
+    step_s = [len(times) / r["value"] for r in samples]
+    ms = 1e3 * sum(step_s) / len(step_s)
+    value = len(times) / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Gaussian blobs)", "impl": "reference",
+        "config": {"workload": WORKLOAD, "grid": [N, N], "solves_per_step": len(times),
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": samples[0]["sample"]},
+        "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)
+    else:
+        run_ours(args, dist)
+
+
+if __name__ == "__main__":
+    main()

@@ -109,6 +109,10 @@ fs_status fs_wave_solve(fs_plan plan, const void *u0, const void *v0, double c, 
 fs_status fs_state_create(fs_plan plan, const void *u0, const void *v0, fs_stream stream,
                           fs_state *out);
 fs_status fs_state_destroy(fs_state state);
+/* fs_state_reset: forward-transform new initial data into an existing state
+ * (same plan; v0 must be NULL iff the state was created without v0).  No
+ * allocation; stream-ordered like fs_state_create. */
+fs_status fs_state_reset(fs_state state, const void *u0, const void *v0, fs_stream stream);
 
 /* fs_diffusion_advance: u(t) from a kept state, t absolute (>= 0) from the
  * state's initial data: inverse 2D DFT of U0 exp(-D|omega|^2 t)
@@ -131,6 +135,14 @@ int fs_size_supported(int n);
 int fs_radix_plan(int L, int e, int *out, int cap);
 /* Number of this library's kernels launched since load (all threads). */
 uint64_t fs_kernel_launches(void);
+/* Kernel timing: when enabled, every launch is bracketed by CUDA events on its
+ * own stream (adds ~2 event records per launch).  fs_profile_report
+ * synchronises the recorded events and writes, per kernel class, the launch
+ * count and total device time in milliseconds; classes: 0 row R2C, 1 column,
+ * 2 row C2R, 3 factor, 4 small, 5 batch.  Returns the number of classes
+ * written (<= cap).  fs_profile_enable(0) stops recording and clears. */
+fs_status fs_profile_enable(int on);
+int fs_profile_report(uint64_t *counts, double *total_ms, int cap);
 
 #ifdef __cplusplus
 }

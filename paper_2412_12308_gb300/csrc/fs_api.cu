@@ -459,6 +459,21 @@ fs_status fs_state_create(fs_plan p, const void *u0, const void *v0, fs_stream s
   return FS_OK;
 }
 
+fs_status fs_state_reset(fs_state s, const void *u0, const void *v0, fs_stream stream) {
+  if (!s || !u0) return set_error(FS_ERR_ARG, "fs_state_reset: NULL argument");
+  if ((v0 != nullptr) != s->has_v)
+    return set_error(FS_ERR_ARG, "fs_state_reset: v0 presence must match the state");
+  fs_plan p = s->plan;
+  Desc d = base_desc(p);
+  d.op = OP_FORWARD;
+  d.flags = v0 ? F_HAS_V0 : 0;
+  d.in_u = u0;
+  d.in_v = v0;
+  d.st_out_u = s->su;
+  d.st_out_v = s->sv;
+  return run(p, d, stream, "fs_state_reset");
+}
+
 fs_status fs_state_destroy(fs_state s) {
   if (!s) return FS_OK;
   cudaDeviceSynchronize();

@@ -10,6 +10,22 @@ namespace fs {
 
 extern std::atomic<unsigned long long> g_launches;
 
+// Optional per-launch event timing (fs_profile_enable); classes as in fsolve.h.
+enum ProfClass { PC_R2C = 0, PC_COL = 1, PC_C2R = 2, PC_FACTOR = 3, PC_SMALL = 4, PC_BATCH = 5, PC_N = 6 };
+bool prof_on();
+void prof_begin(int cls, cudaStream_t s, void **tok);
+void prof_end(void *tok, cudaStream_t s);
+struct ProfScope {
+  void *tok = nullptr;
+  cudaStream_t s;
+  ProfScope(int cls, cudaStream_t st) : s(st) {
+    if (prof_on()) prof_begin(cls, st, &tok);
+  }
+  ~ProfScope() {
+    if (tok) prof_end(tok, s);
+  }
+};
+
 constexpr int kMaxThreads = 512;
 constexpr int kFactorPerUnit = 256;  // factor-table entries per factor unit
 
@@ -177,10 +193,11 @@ struct Launch {
   }
 
   static cudaError_t launch(PassKernel k, int grid, int threads, size_t sm, const Desc &d,
-                            cudaStream_t s) {
+                            cudaStream_t s, int cls) {
     if (!k) return cudaErrorInvalidConfiguration;
     cudaError_t e = set_smem((const void *)k, sm);
     if (e != cudaSuccess) return e;
+    ProfScope ps(cls, s);
     k<<<grid, threads, sm, s>>>(d);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
@@ -188,18 +205,19 @@ struct Launch {
   // forward pass over the real field(s): fields = 1 or 2
   static cudaError_t rows(const Desc &d, int fields, cudaStream_t s) {
     return launch(pass_kernels<T>(d.rp_row.e).r2c, d.n_row_units * fields, row_threads(d),
-                  row_smem(d), d, s);
+                  row_smem(d), d, s, PC_R2C);
   }
   static cudaError_t cols(const Desc &d, cudaStream_t s) {
     const PassKernels pk = pass_kernels<T>(d.rp_col.e);
     return launch(col_two_fields(d) ? pk.col2 : pk.col1, d.n_col_units, col_threads(d),
-                  col_smem(d), d, s);
+                  col_smem(d), d, s, PC_COL);
   }
   static cudaError_t c2r(const Desc &d, int fields, cudaStream_t s) {
     return launch(pass_kernels<T>(d.rp_row.e).c2r, d.n_row_units * fields, row_threads(d),
-                  row_smem(d), d, s);
+                  row_smem(d), d, s, PC_C2R);
   }
   static cudaError_t factor(const Desc &d, cudaStream_t s) {
+    ProfScope ps(PC_FACTOR, s);
     k_factor<T><<<d.n_fac_units, 256, 0, s>>>(d);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
@@ -208,6 +226,7 @@ struct Launch {
     const size_t sm = small_smem(d);
     cudaError_t e = set_smem((const void *)k_small<T>, sm);
     if (e != cudaSuccess) return e;
+    ProfScope ps(PC_SMALL, s);
     k_small<T><<<1, small_threads(d), sm, s>>>(d);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
@@ -216,6 +235,7 @@ struct Launch {
                            int grid, size_t smem, unsigned long long wait_ns, cudaStream_t s) {
     cudaError_t e = set_smem((const void *)k_batch<T>, smem);
     if (e != cudaSuccess) return e;
+    ProfScope ps(PC_BATCH, s);
     k_batch<T><<<grid, kMaxThreads, smem, s>>>(descs, units, n_units, ctl, done, wait_ns);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();

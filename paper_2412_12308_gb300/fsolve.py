@@ -43,13 +43,19 @@ _SIGS = {
     "fs_wave_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_state_create": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "fs_state_destroy": (ctypes.c_int, [_vp]),
+    "fs_state_reset": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "fs_diffusion_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
     "fs_last_error": (ctypes.c_char_p, []),
     "fs_size_supported": (ctypes.c_int, [ctypes.c_int]),
     "fs_radix_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "fs_kernel_launches": (ctypes.c_uint64, []),
+    "fs_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "fs_profile_report": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_int]),
 }
+
+PROFILE_CLASSES = ("row_r2c", "column", "row_c2r", "factor", "small", "batch")
 
 _lib = None
 
@@ -160,6 +166,11 @@ def fs_state_destroy(state):
     _check(_lib.fs_state_destroy(state), "fs_state_destroy")
 
 
+def fs_state_reset(state, u0, v0=None, stream=None):
+    load()
+    _check(_lib.fs_state_reset(state, _ptr(u0), _ptr(v0), _stream(stream)), "fs_state_reset")
+
+
 def fs_diffusion_advance(state, D, t, u_out, stream=None):
     load()
     _check(_lib.fs_diffusion_advance(state, float(D), float(t), _ptr(u_out), _stream(stream)),
@@ -193,3 +204,18 @@ def fs_radix_plan(L, e):
 def fs_kernel_launches():
     load()
     return int(_lib.fs_kernel_launches())
+
+
+def fs_profile_enable(on):
+    load()
+    _check(_lib.fs_profile_enable(1 if on else 0), "fs_profile_enable")
+
+
+def fs_profile_report():
+    """{class name: (launches, total device ms)} of the recorded launches."""
+    load()
+    n = len(PROFILE_CLASSES)
+    counts = (ctypes.c_uint64 * n)()
+    ms = (ctypes.c_double * n)()
+    k = _lib.fs_profile_report(counts, ms, n)
+    return {PROFILE_CLASSES[i]: (int(counts[i]), float(ms[i])) for i in range(k)}
