@@ -126,6 +126,27 @@ fs_status fs_diffusion_advance(fs_state state, double D, double t, void *u_out, 
 fs_status fs_wave_advance(fs_state state, double c, double t, void *u_out, void *v_out,
                           fs_stream stream);
 
+/* ---------------------------------------------------------------- no allocation
+ * fs_poisson_solve_static: the same FP32 Poisson solve as fs_poisson_solve,
+ * for callers that may not allocate device memory while they run (code
+ * hosted in an application that owns the device memory pool, loops where an
+ * allocation's implicit device synchronisation is not acceptable, programs
+ * that size all device memory at start-up).  It needs no plan and allocates
+ * nothing: its scratch (work spectrum and tables) is one fixed device array
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits (about 4.2 MB).  The paper has no counterpart; this is a
+ * deployment variant.
+ *   f, u  device float [ny][nx] (u may alias f); Lx, Ly > 0.
+ *   Sizes as for plans, and nx, ny <= 1024; larger grids: FS_ERR_SIZE.
+ *   The first call on each device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents, so calls
+ *   whose GPU work can overlap (different streams or host threads on one
+ *   device) race; serialise them.  Nothing in it needs to start zeroed.
+ *   Errors: FS_ERR_ARG, FS_ERR_SIZE, FS_ERR_CUDA, FS_ERR_NODEV. */
+fs_status fs_poisson_solve_static(int nx, int ny, double lx, double ly, const void *f, void *u,
+                                  fs_stream stream);
+
 /* ---------------------------------------------------------------- misc */
 const char *fs_last_error(void);
 /* Size rule used by every entry point: 1 if n is supported, else 0. */

@@ -147,6 +147,13 @@ static TileConfig make_tiles(int nx, int ny, const RadixPlan &rr, const RadixPla
   return t;
 }
 
+bool plan_geometry(int nx, int ny, bool f64, RadixPlan *rr, RadixPlan *rc, TileConfig *tc) {
+  if (!size_supported(nx) || !size_supported(ny)) return false;
+  if (!make_rp(nx / 2, f64, rr) || !make_rp(ny, f64, rc)) return false;
+  *tc = make_tiles(nx, ny, *rr, *rc, f64 ? 2 * sizeof(double) : 2 * sizeof(float));
+  return true;
+}
+
 Desc base_desc(const fs_plan_s *p) {
   Desc d;
   memset(&d, 0, sizeof d);

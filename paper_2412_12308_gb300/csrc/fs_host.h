@@ -54,6 +54,8 @@ struct fs_state_s {
 };
 
 namespace fs {
+// Radix plans and tile shapes for an nx x ny grid (false: unsupported size).
+bool plan_geometry(int nx, int ny, bool f64, RadixPlan *rr, RadixPlan *rc, TileConfig *tc);
 // Descriptor with the plan's geometry, tables and tile shapes filled in.
 Desc base_desc(const fs_plan_s *p);
 size_t fac_bytes(const fs_plan_s *p);

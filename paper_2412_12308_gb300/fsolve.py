@@ -39,6 +39,8 @@ _SIGS = {
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_size_t)]),
     "fs_poisson_solve": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "fs_poisson_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               _vp, _vp, _vp]),
     "fs_diffusion_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_state_create": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
@@ -139,6 +141,12 @@ def fs_plan_info(plan):
 def fs_poisson_solve(plan, f, u, stream=None):
     load()
     _check(_lib.fs_poisson_solve(plan, _ptr(f), _ptr(u), _stream(stream)), "fs_poisson_solve")
+
+
+def fs_poisson_solve_static(nx, ny, lx, ly, f, u, stream=None):
+    load()
+    _check(_lib.fs_poisson_solve_static(int(nx), int(ny), float(lx), float(ly), _ptr(f), _ptr(u),
+                                        _stream(stream)), "fs_poisson_solve_static")
 
 
 def fs_diffusion_solve(plan, u0, D, t, u, stream=None):
