@@ -126,6 +126,52 @@ fs_status fs_diffusion_advance(fs_state state, double D, double t, void *u_out, 
 fs_status fs_wave_advance(fs_state state, double c, double t, void *u_out, void *v_out,
                           fs_stream stream);
 
+/* ---------------------------------------------------------------- batches
+ * A request of a batch.  op: one of FS_OP_*.  The solve ops read `in_u`
+ * (and `in_v` for FS_OP_WAVE, may be NULL) and write `out_u`; the advance ops
+ * read `state` and write `out_u` (and `out_v` for FS_OP_WAVE_ADVANCE, may be
+ * NULL).  `plan` gives the grid; every plan in a batch must have the same
+ * dtype.  Pointers are device pointers owned by the caller.
+ */
+enum {
+  FS_OP_POISSON = 0,
+  FS_OP_DIFFUSION = 1,
+  FS_OP_WAVE = 2,
+  FS_OP_DIFFUSION_ADVANCE = 3,
+  FS_OP_WAVE_ADVANCE = 4
+};
+
+typedef struct fs_request {
+  int op;
+  fs_plan plan;
+  fs_state state;
+  const void *in_u;
+  const void *in_v;
+  void *out_u;
+  void *out_v;
+  double D, c, t;
+} fs_request;
+
+/* fs_batch_submit: run n independent requests (any mix of sizes, operators
+ * and kept states; Sec. III solves applied to many problems at once) as ONE
+ * persistent kernel launch, captured in a CUDA graph and replayed when the
+ * same batch shape repeats.  The launch's CTAs pull work units (diffusion
+ * factor ranges, row tiles, column groups, C2R tiles, whole small problems)
+ * from a device work table through an atomic counter; a unit waits (bounded:
+ * 2 s per wait by default, env FS_BATCH_WAIT_NS; expiry sets FS_ERR_TIMEOUT in
+ * the batch status and the kernel exits) only for units of its own problem
+ * listed before it.  Workspace comes from a library-owned arena per in-flight
+ * batch.  Each problem's result depends only on its own request (same tile
+ * shapes and unit code alone or in any mix), so it is bit-identical across
+ * batches.  The call enqueues on `stream` and returns; *ticket_out names the
+ * batch for fs_batch_wait.  Errors: FS_ERR_ARG, FS_ERR_SIZE (mixed dtypes),
+ * FS_ERR_NOMEM, FS_ERR_CUDA.
+ */
+fs_status fs_batch_submit(const fs_request *reqs, int n, uint64_t *ticket_out, fs_stream stream);
+/* Block until batch `ticket` finished (bounded by timeout_us; <0 = no bound);
+ * returns the batch's device status (FS_OK or FS_ERR_TIMEOUT) or a wait error. */
+fs_status fs_batch_wait(uint64_t ticket, int timeout_us);
+
 /* ---------------------------------------------------------------- no allocation
  * fs_poisson_solve_static: the same FP32 Poisson solve as fs_poisson_solve,
  * for callers that may not allocate device memory while they run (code

@@ -1,0 +1,459 @@
+// fs_batch.cu -- the batch executor: many independent solves / advances in
+// one persistent launch (k_batch), replayed from a CUDA graph when the batch
+// shape repeats.
+//
+// Host side: build one Desc per request (geometry from its plan, workspace
+// carved from the slot's arena), then a work table of units.  The order of
+// the table is a three-stage software pipeline over chunks of problems
+// (largest problems first): factor/row/small units of chunk i, column units
+// of chunk i-1, C2R units of chunk i-2.  Every dependency (columns need the
+// problem's rows and factors, C2R needs its columns) therefore points to an
+// earlier table index, so the persistent CTAs that take indices in order
+// never wait on work nobody has started, and each chunk's intermediate
+// spectra are consumed while still resident in L2.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "fs_batch.h"
+#include "fs_kernels.cuh"
+
+extern template struct fs::Launch<float>;
+extern template struct fs::Launch<double>;
+
+namespace fs {
+
+namespace {
+
+constexpr size_t kChunkBytes = 24u << 20;     // intermediate bytes per pipeline chunk
+constexpr size_t kMaxDynSmem = 227u * 1024u;  // per-CTA dynamic shared memory limit
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+long long env_ll(const char *name, long long dflt) {
+  const char *v = getenv(name);
+  return v && *v ? atoll(v) : dflt;
+}
+
+struct Slot {
+  int device = -1;
+  cudaEvent_t ev = nullptr;
+  cudaStream_t cap = nullptr;
+  uint64_t ticket = 0;
+  bool pending = false;
+  Desc *d_descs = nullptr;
+  int4 *d_units = nullptr;
+  int *d_ctl = nullptr;
+  int *d_done = nullptr;
+  char *d_arena = nullptr;
+  size_t cap_descs = 0, cap_units = 0, cap_arena = 0;
+  Desc *h_descs = nullptr;
+  int4 *h_units = nullptr;
+  int *h_status = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int key_descs = -1, key_units = -1, key_grid = -1, key_dtype = -1;
+  size_t key_smem = 0;
+  unsigned long long key_wait = 0;
+};
+
+std::mutex g_mu;
+std::vector<Slot *> g_slots;
+uint64_t g_next_ticket = 1;
+std::deque<std::pair<uint64_t, int>> g_finished;  // recent (ticket, status)
+
+void remember(uint64_t ticket, int status) {
+  g_finished.emplace_back(ticket, status);
+  while (g_finished.size() > 4096) g_finished.pop_front();
+}
+
+// Grow a device + pinned-host buffer pair (slot idle).
+template <typename X>
+cudaError_t grow(X **d, X **h, size_t &cap, size_t need) {
+  if (need <= cap) return cudaSuccess;
+  size_t n = std::max(need, cap * 2);
+  cudaFree(*d);
+  if (h) cudaFreeHost(*h);
+  *d = nullptr;
+  if (h) *h = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc((void **)d, n * sizeof(X));
+  if (e == cudaSuccess && h) e = cudaMallocHost((void **)h, n * sizeof(X));
+  if (e == cudaSuccess) cap = n;
+  return e;
+}
+
+void drop_graph(Slot *s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  s->key_descs = -1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- planning
+fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp) {
+  bp->descs.clear();
+  bp->units.clear();
+  bp->arena_bytes = 0;
+  bp->smem = 0;
+  bp->dtype = -1;
+  struct Item {
+    int idx;
+    double cost;
+    size_t ws;
+  };
+  std::vector<Item> items;
+  std::vector<size_t> ws_off(n);
+  std::vector<Desc> ds(n);
+  for (int i = 0; i < n; ++i) {
+    const fs_request &r = reqs[i];
+    fs_plan p = r.plan;
+    if ((r.op == FS_OP_DIFFUSION_ADVANCE || r.op == FS_OP_WAVE_ADVANCE)) {
+      if (!r.state) return set_error(FS_ERR_ARG, "fs_batch_submit: advance request without a state");
+      p = r.state->plan;
+    }
+    if (!p) return set_error(FS_ERR_ARG, "fs_batch_submit: request without a plan");
+    if (!r.out_u) return set_error(FS_ERR_ARG, "fs_batch_submit: request without an output");
+    if (bp->dtype < 0) bp->dtype = p->dtype;
+    if (bp->dtype != p->dtype) return set_error(FS_ERR_SIZE, "fs_batch_submit: mixed dtypes in one batch");
+    Desc d = base_desc(p);
+    d.work_u = d.work_v = nullptr;
+    d.fac = nullptr;
+    d.out_u = r.out_u;
+    switch (r.op) {
+      case FS_OP_POISSON:
+        if (!r.in_u) return set_error(FS_ERR_ARG, "fs_batch_submit: Poisson without input");
+        d.op = OP_POISSON;
+        d.in_u = r.in_u;
+        break;
+      case FS_OP_DIFFUSION:
+      case FS_OP_DIFFUSION_ADVANCE:
+        if (!(r.D >= 0.0) || !(r.t >= 0.0) || !std::isfinite(r.D * r.t))
+          return set_error(FS_ERR_ARG, "fs_batch_submit: diffusion needs finite D >= 0, t >= 0");
+        d.p_dt = r.D * r.t;
+        d.p_t = r.t;
+        if (r.op == FS_OP_DIFFUSION) {
+          if (!r.in_u) return set_error(FS_ERR_ARG, "fs_batch_submit: diffusion without input");
+          d.op = OP_DIFFUSION;
+          d.in_u = r.in_u;
+        } else {
+          d.op = OP_DIFF_ADV;
+          d.st_u = r.state->su;
+        }
+        break;
+      case FS_OP_WAVE:
+      case FS_OP_WAVE_ADVANCE:
+        if (!(r.c > 0.0) || !std::isfinite(r.c) || !std::isfinite(r.t))
+          return set_error(FS_ERR_ARG, "fs_batch_submit: wave needs finite c > 0 and t");
+        d.p_c = r.c;
+        d.p_t = r.t;
+        if (r.op == FS_OP_WAVE) {
+          if (!r.in_u) return set_error(FS_ERR_ARG, "fs_batch_submit: wave without input");
+          d.op = OP_WAVE;
+          d.in_u = r.in_u;
+          d.in_v = r.in_v;
+          d.flags = r.in_v ? F_HAS_V0 : 0;
+        } else {
+          d.op = OP_WAVE_ADV;
+          d.st_u = r.state->su;
+          d.st_v = r.state->sv;
+          d.flags = (r.state->has_v ? F_HAS_V0 : 0) | (r.out_v ? F_WANT_V : 0);
+          d.out_v = r.out_v;
+        }
+        break;
+      default:
+        return set_error(FS_ERR_ARG, "fs_batch_submit: unknown op");
+    }
+    const bool diff = d.op == OP_DIFFUSION || d.op == OP_DIFF_ADV;
+    const int nspec = small_nspec(d);
+    const size_t small_b = nspec == 2 ? p->tc.small_smem2 : p->tc.small_smem1;
+    const long long small_max = env_ll("FS_BATCH_SMALL_MAX", 256LL * 256LL);
+    d.small = (small_b > 0 && small_b <= kMaxDynSmem && (long long)p->nx * p->ny <= small_max) ? 1 : 0;
+    size_t ws = 0;
+    if (diff) ws += align256(fac_bytes(p));
+    if (!d.small) {
+      ws += align256(p->spec_bytes);
+      const bool need_v = (d.op == OP_WAVE && (d.flags & F_HAS_V0)) ||
+                          (d.op == OP_WAVE_ADV && (d.flags & F_WANT_V));
+      if (need_v) ws += align256(p->spec_bytes);
+    }
+    ws_off[i] = bp->arena_bytes;
+    bp->arena_bytes += ws;
+    ds[i] = d;
+    // cost ~ bytes moved (3 passes) -> largest first
+    items.push_back({i, (double)p->nx * p->ny * (d.small ? 1.0 : 3.0), ws});
+  }
+  // stable largest-first order
+  std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+  bp->descs.resize(n);
+  std::vector<int> slot_of(n);
+  for (int k = 0; k < n; ++k) {
+    slot_of[items[k].idx] = k;
+    bp->descs[k] = ds[items[k].idx];
+    bp->req_of_desc.push_back(items[k].idx);
+  }
+  bp->ws_off.resize(n);
+  for (int k = 0; k < n; ++k) bp->ws_off[k] = ws_off[items[k].idx];
+
+  // chunks by intermediate bytes
+  std::vector<int> chunk_start;
+  size_t acc = 0;
+  for (int k = 0; k < n; ++k) {
+    if (k == 0 || acc >= kChunkBytes) {
+      chunk_start.push_back(k);
+      acc = 0;
+    }
+    acc += items[k].ws;
+  }
+  chunk_start.push_back(n);
+  const int nch = (int)chunk_start.size() - 1;
+  auto emit_front = [&](int c) {
+    for (int k = chunk_start[c]; k < chunk_start[c + 1]; ++k) {
+      const Desc &d = bp->descs[k];
+      if (d.small) {
+        bp->units.push_back(make_int4(k, K_SMALL, 0, 0));
+        continue;
+      }
+      if (d.op == OP_DIFFUSION || d.op == OP_DIFF_ADV)
+        for (int u = 0; u < d.n_fac_units; ++u) bp->units.push_back(make_int4(k, K_FACTOR, u, 0));
+      if (d.op != OP_DIFF_ADV && d.op != OP_WAVE_ADV) {
+        const int fields = (d.op == OP_WAVE && (d.flags & F_HAS_V0)) ? 2 : 1;
+        for (int f = 0; f < fields; ++f)
+          for (int u = 0; u < d.n_row_units; ++u) bp->units.push_back(make_int4(k, K_ROW, u, f));
+      }
+    }
+  };
+  auto emit_col = [&](int c) {
+    for (int k = chunk_start[c]; k < chunk_start[c + 1]; ++k) {
+      const Desc &d = bp->descs[k];
+      if (d.small) continue;
+      for (int u = 0; u < d.n_col_units; ++u) bp->units.push_back(make_int4(k, K_COL, u, 0));
+    }
+  };
+  auto emit_c2r = [&](int c) {
+    for (int k = chunk_start[c]; k < chunk_start[c + 1]; ++k) {
+      const Desc &d = bp->descs[k];
+      if (d.small) continue;
+      const int fields = (d.op == OP_WAVE_ADV && (d.flags & F_WANT_V)) ? 2 : 1;
+      for (int f = 0; f < fields; ++f)
+        for (int u = 0; u < d.n_row_units; ++u) bp->units.push_back(make_int4(k, K_C2R, u, f));
+    }
+  };
+  for (int i = 0; i < nch + 2; ++i) {
+    if (i < nch) emit_front(i);
+    if (i - 1 >= 0 && i - 1 < nch) emit_col(i - 1);
+    if (i - 2 >= 0 && i - 2 < nch) emit_c2r(i - 2);
+  }
+  return FS_OK;
+}
+
+template <typename T>
+static size_t unit_smem(const Desc &d) {
+  if (d.small) return Launch<T>::small_smem(d);
+  return std::max(Launch<T>::row_smem(d), Launch<T>::col_smem(d));
+}
+
+// Resolve arena offsets into pointers and compute the launch's shared memory.
+template <typename T>
+static size_t finish_descs(BatchPlan *bp, char *arena) {
+  size_t smem = 0;
+  for (size_t k = 0; k < bp->descs.size(); ++k) {
+    Desc &d = bp->descs[k];
+    char *w = arena + bp->ws_off[k];
+    const size_t fb = align256((size_t)(d.M + 1 + d.ny) * 8);  // float2 or double per entry
+    const size_t sb = align256((size_t)(d.M + 1) * d.ny * 2 * sizeof(T));
+    if (d.op == OP_DIFFUSION || d.op == OP_DIFF_ADV) {
+      d.fac = w;
+      w += fb;
+    }
+    if (!d.small) {
+      d.work_u = w;
+      w += sb;
+      const bool need_v = (d.op == OP_WAVE && (d.flags & F_HAS_V0)) ||
+                          (d.op == OP_WAVE_ADV && (d.flags & F_WANT_V));
+      if (need_v) d.work_v = w;
+    }
+    smem = std::max(smem, unit_smem<T>(d));
+  }
+  return smem;
+}
+
+}  // namespace fs
+
+using namespace fs;
+
+static fs_status submit_impl(const fs_request *reqs, int n, uint64_t *ticket_out, cudaStream_t stream) {
+  BatchPlan bp;
+  fs_status st = plan_requests(reqs, n, &bp);
+  if (st != FS_OK) return st;
+  const unsigned long long wait_ns = (unsigned long long)env_ll("FS_BATCH_WAIT_NS", 2000000000LL);
+  const bool inject = env_ll("FS_BATCH_INJECT_STALL", 0) != 0;
+
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: cudaGetDevice");
+  // an idle slot of this device (its last batch finished), else a new one
+  Slot *s = nullptr;
+  for (Slot *c : g_slots) {
+    if (c->device != dev) continue;
+    if (c->pending) {
+      const cudaError_t q = cudaEventQuery(c->ev);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return cuda_error(q, "fs_batch_submit: event query");
+      c->pending = false;
+      remember(c->ticket, c->h_status[1]);
+    }
+    s = c;
+    break;
+  }
+  if (!s) {
+    s = new Slot();
+    s->device = dev;
+    e = cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_status, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_ctl, 2 * sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: slot creation");
+    g_slots.push_back(s);
+  }
+  const size_t nd = bp.descs.size(), nu = bp.units.size();
+  const size_t cd = s->cap_descs;
+  e = grow(&s->d_descs, &s->h_descs, s->cap_descs, nd);
+  if (e == cudaSuccess && s->cap_descs != cd) {
+    cudaFree(s->d_done);
+    s->d_done = nullptr;
+    e = cudaMalloc((void **)&s->d_done, 5 * s->cap_descs * sizeof(int));
+    drop_graph(s);
+  }
+  const size_t cu = s->cap_units;
+  if (e == cudaSuccess) e = grow(&s->d_units, &s->h_units, s->cap_units, nu);
+  if (e == cudaSuccess && s->cap_units != cu) drop_graph(s);
+  if (e == cudaSuccess && bp.arena_bytes > s->cap_arena) {
+    cudaFree(s->d_arena);
+    s->d_arena = nullptr;
+    s->cap_arena = 0;
+    e = cudaMalloc((void **)&s->d_arena, bp.arena_bytes);
+    if (e == cudaSuccess) s->cap_arena = bp.arena_bytes;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: buffer allocation");
+
+  const int dtype = bp.dtype;
+  const size_t smem = dtype == FS_F64 ? finish_descs<double>(&bp, s->d_arena)
+                                      : finish_descs<float>(&bp, s->d_arena);
+  if (smem > kMaxDynSmem) return set_error(FS_ERR_SIZE, "fs_batch_submit: unit shared memory too large");
+  if (inject) {
+    // test hook: make the first three-pass problem's column units wait for a
+    // row tile that is never produced, so the bounded wait expires
+    for (Desc &d : bp.descs)
+      if (!d.small && d.op != OP_DIFF_ADV && d.op != OP_WAVE_ADV) {
+        d.n_row_units += 1;
+        break;
+      }
+  }
+  memcpy(s->h_descs, bp.descs.data(), nd * sizeof(Desc));
+  memcpy(s->h_units, bp.units.data(), nu * sizeof(int4));
+
+  int per_sm = 0, sms = 0;
+  e = dtype == FS_F64 ? Launch<double>::batch_occupancy(smem, &per_sm) : Launch<float>::batch_occupancy(smem, &per_sm);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: occupancy");
+  if (per_sm < 1) return set_error(FS_ERR_SIZE, "fs_batch_submit: batch kernel does not fit on an SM");
+  int grid = sms * per_sm;
+  if ((size_t)grid > nu) grid = (int)nu;
+
+  const bool same = s->gexec && s->key_descs == (int)nd && s->key_units == (int)nu && s->key_grid == grid &&
+                    s->key_dtype == dtype && s->key_smem == smem && s->key_wait == wait_ns;
+  if (!same) {
+    drop_graph(s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaMemcpyAsync(s->d_descs, s->h_descs, nd * sizeof(Desc), cudaMemcpyHostToDevice, s->cap);
+      cudaMemcpyAsync(s->d_units, s->h_units, nu * sizeof(int4), cudaMemcpyHostToDevice, s->cap);
+      cudaMemsetAsync(s->d_ctl, 0, 2 * sizeof(int), s->cap);
+      cudaMemsetAsync(s->d_done, 0, 5 * nd * sizeof(int), s->cap);
+      cudaError_t le = dtype == FS_F64
+                           ? Launch<double>::batch(s->d_descs, s->d_units, (int)nu, s->d_ctl, s->d_done,
+                                                   grid, smem, wait_ns, s->cap)
+                           : Launch<float>::batch(s->d_descs, s->d_units, (int)nu, s->d_ctl, s->d_done,
+                                                  grid, smem, wait_ns, s->cap);
+      cudaMemcpyAsync(s->h_status, s->d_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->cap);
+      e = cudaStreamEndCapture(s->cap, &g);
+      if (e == cudaSuccess && le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      s->gexec = nullptr;
+      return cuda_error(e, "fs_batch_submit: graph capture");
+    }
+    s->key_descs = (int)nd;
+    s->key_units = (int)nu;
+    s->key_grid = grid;
+    s->key_dtype = dtype;
+    s->key_smem = smem;
+    s->key_wait = wait_ns;
+  } else {
+    g_launches.fetch_add(1, std::memory_order_relaxed);  // the replayed k_batch
+  }
+  void *tok = nullptr;
+  if (prof_on()) prof_begin(PC_BATCH, stream, &tok);
+  e = cudaGraphLaunch(s->gexec, stream);
+  if (tok) prof_end(tok, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev, stream);
+  if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: graph launch");
+  s->pending = true;
+  s->ticket = g_next_ticket++;
+  if (ticket_out) *ticket_out = s->ticket;
+  return FS_OK;
+}
+
+extern "C" fs_status fs_batch_submit(const fs_request *reqs, int n, uint64_t *ticket_out, fs_stream stream) {
+  if (ticket_out) *ticket_out = 0;
+  if (!reqs || n <= 0) return set_error(FS_ERR_ARG, "fs_batch_submit: empty batch");
+  return submit_impl(reqs, n, ticket_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" fs_status fs_batch_wait(uint64_t ticket, int timeout_us) {
+  Slot *s = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &f : g_finished)
+      if (f.first == ticket) return f.second == 0 ? FS_OK : set_error((fs_status)f.second, "batch failed");
+    for (Slot *c : g_slots)
+      if (c->ticket == ticket && c->pending) s = c;
+    if (!s) {
+      if (ticket == 0 || ticket >= g_next_ticket) return set_error(FS_ERR_ARG, "fs_batch_wait: unknown ticket");
+      return FS_OK;  // finished long ago
+    }
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(s->ev);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return cuda_error(q, "fs_batch_wait");
+    if (timeout_us >= 0 && std::chrono::duration_cast<std::chrono::microseconds>(
+                               std::chrono::steady_clock::now() - t0).count() > timeout_us)
+      return set_error(FS_ERR_TIMEOUT, "fs_batch_wait: timed out");
+    std::this_thread::yield();
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  int status = 0;
+  if (s->pending && s->ticket == ticket) {
+    s->pending = false;
+    status = s->h_status[1];
+    remember(ticket, status);
+  } else {
+    for (auto &f : g_finished)
+      if (f.first == ticket) status = f.second;
+  }
+  if (status != 0) return set_error((fs_status)status, "fs_batch_wait: a unit's bounded wait expired");
+  return FS_OK;
+}

@@ -235,7 +235,6 @@ struct Launch {
                            int grid, size_t smem, unsigned long long wait_ns, cudaStream_t s) {
     cudaError_t e = set_smem((const void *)k_batch<T>, smem);
     if (e != cudaSuccess) return e;
-    ProfScope ps(PC_BATCH, s);
     k_batch<T><<<grid, kMaxThreads, smem, s>>>(descs, units, n_units, ctl, done, wait_ns);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();

@@ -29,8 +29,18 @@ FS_OP_WAVE = 2
 FS_OP_DIFFUSION_ADVANCE = 3
 FS_OP_WAVE_ADVANCE = 4
 
-# Entry points declared in include/fsolve.h: name -> (restype, argtypes)
 _vp = ctypes.c_void_p
+
+
+class FsRequest(ctypes.Structure):
+    """struct fs_request of include/fsolve.h."""
+
+    _fields_ = [("op", ctypes.c_int), ("plan", _vp), ("state", _vp), ("in_u", _vp), ("in_v", _vp),
+                ("out_u", _vp), ("out_v", _vp), ("D", ctypes.c_double), ("c", ctypes.c_double),
+                ("t", ctypes.c_double)]
+
+
+# Entry points declared in include/fsolve.h: name -> (restype, argtypes)
 _SIGS = {
     "fs_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, ctypes.POINTER(_vp)]),
@@ -48,6 +58,9 @@ _SIGS = {
     "fs_state_reset": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "fs_diffusion_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
+    "fs_batch_submit": (ctypes.c_int, [ctypes.POINTER(FsRequest), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                       _vp]),
+    "fs_batch_wait": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
     "fs_last_error": (ctypes.c_char_p, []),
     "fs_size_supported": (ctypes.c_int, [ctypes.c_int]),
     "fs_radix_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -189,6 +202,29 @@ def fs_wave_advance(state, c, t, u_out, v_out=None, stream=None):
     load()
     _check(_lib.fs_wave_advance(state, float(c), float(t), _ptr(u_out), _ptr(v_out), _stream(stream)),
            "fs_wave_advance")
+
+
+def fs_request(op, plan=None, state=None, in_u=None, in_v=None, out_u=None, out_v=None, D=0.0, c=0.0, t=0.0):
+    """Marshal one batch request (tensors -> device pointers)."""
+
+    def p(x):
+        return None if x is None else (x if isinstance(x, int) else x.data_ptr())
+
+    return FsRequest(int(op), plan, state, p(in_u), p(in_v), p(out_u), p(out_v), float(D), float(c), float(t))
+
+
+def fs_batch_submit(reqs, stream=None):
+    """Submit a list of FsRequest; returns the batch ticket."""
+    load()
+    arr = (FsRequest * len(reqs))(*reqs)
+    ticket = ctypes.c_uint64()
+    _check(_lib.fs_batch_submit(arr, len(reqs), ctypes.byref(ticket), _stream(stream)), "fs_batch_submit")
+    return ticket.value
+
+
+def fs_batch_wait(ticket, timeout_us=-1):
+    load()
+    _check(_lib.fs_batch_wait(ctypes.c_uint64(ticket), int(timeout_us)), "fs_batch_wait")
 
 
 def fs_last_error():

@@ -35,7 +35,7 @@ def lib():
 def test_header_declares_entry_points():
     names = _declared()
     for must in ("fs_plan_create", "fs_poisson_solve", "fs_diffusion_advance", "fs_wave_advance",
-                 "fs_state_create", "fs_last_error"):
+                 "fs_state_create", "fs_batch_submit", "fs_batch_wait", "fs_last_error"):
         assert must in names
 
 
@@ -107,3 +107,12 @@ def test_binding_raises_with_message(lib):
         fsolve.fs_plan_create(10, 7, 1.0, 1.0, fsolve.FS_F32)
     assert ei.value.status == -2
     assert "unsupported size" in str(ei.value)
+
+
+def test_batch_rejects_bad_requests_on_host(lib):
+    assert lib.fs_batch_submit(None, 0, None, None) == -1
+    r = fsolve.FsRequest(0, None, None, None, None, None, None, 0.0, 0.0, 0.0)
+    arr = (fsolve.FsRequest * 1)(r)
+    t = ctypes.c_uint64()
+    assert lib.fs_batch_submit(arr, 1, ctypes.byref(t), None) == -1  # no plan
+    assert lib.fs_batch_wait(12345678, 0) == -1  # unknown ticket

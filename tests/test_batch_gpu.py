@@ -1,0 +1,190 @@
+"""Batch executor (one persistent launch per batch) on the GPU.
+
+Checks: every problem of an uneven mixed batch matches the float64 oracle
+(rel-L2 <= 1e-5; normwise for strongly decayed diffusion outputs); a request's
+result is bit-identical alone and in a mix; batched results agree with the
+per-call entry points; a repeated batch shape replays its CUDA graph with the
+same results; and an injected dependency that never completes ends the
+launch through the bounded wait with FS_ERR_TIMEOUT, leaving the context
+usable.
+"""
+
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2412_12308_gb300 import fsolve, workloads as wl
+
+pytestmark = pytest.mark.gpu
+F32 = fsolve.FS_F32
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+class Problems:
+    """Device inputs/outputs and plans for a list of workloads.Problem."""
+
+    def __init__(self, probs, dtype=F32):
+        self.probs = probs
+        self.dtype = dtype
+        self.tdt = torch.float32 if dtype == F32 else torch.float64
+        self.plans = {}
+        self.inputs, self.outputs = [], []
+        for p in probs:
+            if p.n not in self.plans:
+                self.plans[p.n] = fsolve.fs_plan_create(p.n, p.n, p.lx, p.ly, dtype)
+            f = p.field(np.float64).astype(np.float32 if dtype == F32 else np.float64)
+            self.inputs.append(torch.tensor(f, device="cuda"))
+            self.outputs.append(torch.full_like(self.inputs[-1], float("nan")))
+
+    def requests(self, idx=None):
+        out = []
+        for i in (range(len(self.probs)) if idx is None else idx):
+            p = self.probs[i]
+            op = {"poisson": fsolve.FS_OP_POISSON, "diffusion": fsolve.FS_OP_DIFFUSION,
+                  "wave": fsolve.FS_OP_WAVE}[p.op]
+            out.append(fsolve.fs_request(op, plan=self.plans[p.n], in_u=self.inputs[i], out_u=self.outputs[i],
+                                         D=p.D, c=p.c, t=p.t))
+        return out
+
+    def close(self):
+        for h in self.plans.values():
+            fsolve.fs_plan_destroy(h)
+
+
+def oracle_of(p, f64):
+    if p.op == "poisson":
+        return oracle.poisson(f64, p.lx, p.ly)
+    if p.op == "diffusion":
+        return oracle.diffusion(f64, p.D, p.t, p.lx, p.ly)
+    return oracle.wave(f64, None, p.c, p.t, p.lx, p.ly)
+
+
+def check_vs_oracle(P, i, got):
+    p = P.probs[i]
+    f = P.inputs[i].double().cpu().numpy()
+    want = oracle_of(p, f)
+    den = np.linalg.norm(want)
+    if p.op == "diffusion":
+        den = max(den, np.linalg.norm(f))
+    return float(np.linalg.norm(got - want) / den)
+
+
+def test_mixed_batch_vs_oracle_and_alone(gpu_lib):
+    probs = wl.batch_mix(seed=99, count=48, sizes=(64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768))
+    P = Problems(probs)
+    try:
+        t = fsolve.fs_batch_submit(P.requests())
+        fsolve.fs_batch_wait(t, 30_000_000)
+        mixed = [o.clone() for o in P.outputs]
+        for i in range(len(probs)):
+            err = check_vs_oracle(P, i, mixed[i].double().cpu().numpy())
+            assert err <= 1e-5, (i, probs[i].op, probs[i].n, err)
+        # each request alone in its own batch: bit-identical
+        for i in range(0, len(probs), 5):
+            P.outputs[i].fill_(float("nan"))
+            t = fsolve.fs_batch_submit(P.requests([i]))
+            fsolve.fs_batch_wait(t, 30_000_000)
+            assert torch.equal(P.outputs[i], mixed[i]), (i, probs[i].op, probs[i].n)
+        # replay of the same batch shape (cached graph): same results
+        for o in P.outputs:
+            o.fill_(float("nan"))
+        t = fsolve.fs_batch_submit(P.requests())
+        fsolve.fs_batch_wait(t, 30_000_000)
+        for i in range(len(probs)):
+            assert torch.equal(P.outputs[i], mixed[i])
+    finally:
+        P.close()
+
+
+def test_batch_matches_per_call_entry_points(gpu_lib):
+    probs = wl.batch_mix(seed=7, count=12, sizes=(64, 128, 256, 512, 1024))
+    P = Problems(probs)
+    try:
+        t = fsolve.fs_batch_submit(P.requests())
+        fsolve.fs_batch_wait(t, 30_000_000)
+        for i, p in enumerate(probs):
+            ref = torch.empty_like(P.outputs[i])
+            h = P.plans[p.n]
+            if p.op == "poisson":
+                fsolve.fs_poisson_solve(h, P.inputs[i], ref)
+            elif p.op == "diffusion":
+                fsolve.fs_diffusion_solve(h, P.inputs[i], p.D, p.t, ref)
+            else:
+                fsolve.fs_wave_solve(h, P.inputs[i], None, p.c, p.t, ref)
+            torch.cuda.synchronize()
+            d = float((P.outputs[i].double() - ref.double()).norm())
+            den = max(float(ref.double().norm()), float(P.inputs[i].double().norm()) * 1e-2)
+            assert d / den <= 1e-6, (i, p.op, p.n, d / den)
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_batched_advances_from_kept_states(gpu_lib, dtype):
+    tdt = torch.float32 if dtype == 0 else torch.float64
+    tol = 1e-5 if dtype == 0 else 1e-12
+    n, lx = 256, 2 * np.pi
+    u0, blobs, _, D, times = wl.diffusion_blobs_1024(n=n, n_times=12)
+    v0 = np.random.default_rng(2).standard_normal((n, n)) * 0.1
+    u0 = u0.astype(np.float32).astype(np.float64)
+    v0 = v0.astype(np.float32).astype(np.float64)
+    plan = fsolve.fs_plan_create(n, n, lx, lx, dtype)
+    ud, vd = torch.tensor(u0, dtype=tdt, device="cuda"), torch.tensor(v0, dtype=tdt, device="cuda")
+    s1 = fsolve.fs_state_create(plan, ud)
+    s2 = fsolve.fs_state_create(plan, ud, vd)
+    try:
+        outs, reqs = [], []
+        for t in times:
+            o = torch.empty_like(ud)
+            outs.append(("diff", float(t), o, None))
+            reqs.append(fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, state=s1, out_u=o, D=D, t=float(t)))
+        for t in times[::3]:
+            o, ov = torch.empty_like(ud), torch.empty_like(ud)
+            outs.append(("wave", float(t), o, ov))
+            reqs.append(fsolve.fs_request(fsolve.FS_OP_WAVE_ADVANCE, state=s2, out_u=o, out_v=ov, c=1.3, t=float(t)))
+        tk = fsolve.fs_batch_submit(reqs)
+        fsolve.fs_batch_wait(tk, 30_000_000)
+        F, G = oracle.state_spectrum(u0), oracle.state_spectrum(v0)
+        for kind, t, o, ov in outs:
+            if kind == "diff":
+                want = np.real(oracle.idft2(oracle.diffusion_spectrum(F, D, t, lx, lx)))
+                assert rel(o.cpu().numpy(), want) <= tol, (kind, t)
+            else:
+                U, V = oracle.wave_spectrum(F, G, 1.3, t, lx, lx)
+                assert rel(o.cpu().numpy(), np.real(oracle.idft2(U))) <= tol, (kind, t)
+                assert rel(ov.cpu().numpy(), np.real(oracle.idft2(V))) <= tol, (kind, t)
+    finally:
+        fsolve.fs_state_destroy(s1)
+        fsolve.fs_state_destroy(s2)
+        fsolve.fs_plan_destroy(plan)
+
+
+def test_bounded_wait_expires_without_fault(gpu_lib, monkeypatch):
+    probs = wl.batch_mix(seed=5, count=6, sizes=(512, 1024))
+    P = Problems(probs)
+    try:
+        monkeypatch.setenv("FS_BATCH_INJECT_STALL", "1")
+        monkeypatch.setenv("FS_BATCH_WAIT_NS", str(20_000_000))  # 20 ms
+        t = fsolve.fs_batch_submit(P.requests())
+        with pytest.raises(fsolve.FsError) as ei:
+            fsolve.fs_batch_wait(t, 30_000_000)
+        assert ei.value.status == -6  # FS_ERR_TIMEOUT
+        monkeypatch.delenv("FS_BATCH_INJECT_STALL")
+        monkeypatch.delenv("FS_BATCH_WAIT_NS")
+        # the context is still usable and results are right afterwards
+        for o in P.outputs:
+            o.fill_(float("nan"))
+        t = fsolve.fs_batch_submit(P.requests())
+        fsolve.fs_batch_wait(t, 30_000_000)
+        for i in range(len(probs)):
+            assert check_vs_oracle(P, i, P.outputs[i].double().cpu().numpy()) <= 1e-5
+    finally:
+        P.close()
