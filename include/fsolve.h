@@ -200,6 +200,12 @@ int fs_size_supported(int n);
 /* Radix factorisation used for a length-L transform with `e` elements per
  * thread: writes up to `cap` radices into out, returns the count (0: none). */
 int fs_radix_plan(int L, int e, int *out, int cap);
+/* Device error word of the bounded waits inside the kernels (a TMA copy
+ * that did not complete within 1 s makes the kernel record an error and
+ * return instead of waiting forever).  Synchronises the device, writes the
+ * code (0 = none) to *code when non-NULL, clears it, and returns
+ * FS_ERR_TIMEOUT if it was set. */
+fs_status fs_device_status(int *code);
 /* Number of this library's kernels launched since load (all threads). */
 uint64_t fs_kernel_launches(void);
 /* Kernel timing: when enabled, every launch is bracketed by CUDA events on its

@@ -1,0 +1,121 @@
+"""Named solver workloads for timing and profiling (CUDA path only).
+
+    python -m paper_2412_12308_gb300.cases poisson --n 4096 --iters 20
+    python -m paper_2412_12308_gb300.cases wave_adv --n 4096 --iters 20
+    python -m paper_2412_12308_gb300.cases diffusion_batch --n 1024 --iters 5
+
+Each case runs `--warmup` untimed repetitions, then `--iters` timed ones
+(CUDA events on the current stream) and prints one JSON line with the mean
+time per repetition, the per-kernel averages from the library's event
+profiler and the algorithmic HBM bytes per repetition.  Inputs are seeded
+synthetic fields (workloads.py); no result is checked here (the tests do
+that).  Used for ncu captures: pick kernels with `-k regex:...`.
+"""
+
+import argparse
+import json
+
+import numpy as np
+
+
+def _setup(n, dtype, lx=1.0):
+    import torch
+
+    from . import fsolve, workloads
+
+    fsolve.load()
+    rng = np.random.default_rng(n)
+    f = workloads.mode_sum(workloads.draw_modes(rng, 8, 16), n, n, lx, lx)
+    tdt = torch.float32 if dtype == fsolve.FS_F32 else torch.float64
+    fd = torch.tensor(f, dtype=tdt, device="cuda")
+    plan = fsolve.fs_plan_create(n, n, lx, lx, dtype)
+    return fsolve, plan, fd
+
+
+def run(case, n, iters, warmup, dtype=0, profile=True):
+    import torch
+
+    from . import fsolve as fs
+
+    fsolve, plan, fd = _setup(n, dtype)
+    out = torch.empty_like(fd)
+    esz = fd.element_size()
+    spec = (n // 2 + 1) * n * 2 * esz
+    real = n * n * esz
+    state = None
+    extra = {}
+    if case == "poisson":
+        def rep():
+            fsolve.fs_poisson_solve(plan, fd, out)
+        algo = 3 * (real + spec)  # three passes: R2C, column, C2R
+    elif case == "wave_solve":
+        def rep():
+            fsolve.fs_wave_solve(plan, fd, None, 1.0, 0.37, out)
+        algo = 3 * (real + spec)
+    elif case == "wave_adv":
+        state = fsolve.fs_state_create(plan, fd)
+
+        def rep():
+            fsolve.fs_wave_advance(state, 1.0, 0.37, out)
+        algo = 2 * spec + spec + real  # column (read kept, write work) + C2R
+    elif case == "diffusion_adv":
+        state = fsolve.fs_state_create(plan, fd)
+
+        def rep():
+            fsolve.fs_diffusion_advance(state, 0.1, 0.37, out)
+        algo = 2 * spec + spec + real
+    elif case == "diffusion_batch":
+        nt = 100
+        state = fsolve.fs_state_create(plan, fd)
+        outs = torch.empty((nt, n, n), dtype=fd.dtype, device="cuda")
+        reqs = [fs.fs_request(fs.FS_OP_DIFFUSION_ADVANCE, state=state, out_u=outs[j], D=0.1, t=j / (nt - 1))
+                for j in range(nt)]
+
+        def rep():
+            fsolve.fs_state_reset(state, fd)
+            fsolve.fs_batch_submit(reqs)
+        algo = (real + 2 * spec) + nt * (3 * spec + real)
+        extra["solves_per_rep"] = nt
+    else:
+        raise SystemExit(f"unknown case {case}")
+    for _ in range(warmup):
+        rep()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(iters):
+        rep()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / iters
+    res = {"case": case, "n": n, "dtype": dtype, "iters": iters, "ms_per_rep": round(ms, 5),
+           "algorithmic_bytes": algo, "algorithmic_GBps": round(algo / (ms / 1e3) / 1e9, 1)}
+    res.update(extra)
+    if profile:
+        fsolve.fs_profile_enable(True)
+        for _ in range(iters):
+            rep()
+        torch.cuda.synchronize()
+        prof = fsolve.fs_profile_report()
+        fsolve.fs_profile_enable(False)
+        res["per_kernel_us"] = {k: round(1e3 * v[1] / v[0], 3) for k, v in prof.items() if v[0]}
+    if state is not None:
+        fsolve.fs_state_destroy(state)
+    fsolve.fs_plan_destroy(plan)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--f64", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    a = ap.parse_args()
+    print(json.dumps(run(a.case, a.n, a.iters, a.warmup, 1 if a.f64 else 0, not a.no_profile)))
+
+
+if __name__ == "__main__":
+    main()

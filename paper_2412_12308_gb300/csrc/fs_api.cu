@@ -8,6 +8,7 @@
 
 #include "fs_host.h"
 #include "fs_kernels.cuh"
+#include "fs_tma.cuh"
 
 // The kernels are instantiated in fs_kernels_f32.cu / fs_kernels_f64.cu.
 extern template struct fs::Launch<float>;
@@ -16,6 +17,14 @@ extern template struct fs::Launch<double>;
 namespace fs {
 
 std::atomic<unsigned long long> g_launches{0};
+
+bool tma_enabled() {
+  static const bool on = [] {
+    const char *v = getenv("FS_NO_TMA");
+    return !(v && *v && *v != '0');
+  }();
+  return on;
+}
 
 static thread_local std::string t_last_error;
 
@@ -115,6 +124,9 @@ static TileConfig make_tiles(int nx, int ny, const RadixPlan &rr, const RadixPla
   int cc = 32;
   while (cc > 1 && (cc * tcl > kMaxThreads || cs * padded_len(cc * ny) > lim)) cc >>= 1;
   t.cols_per_unit = cc;
+  // FP32 power-of-two lengths: the tile shapes of the compile-time kernels
+  if (cs == 8 && rr.e == 16 && p2_row_ok(M)) t.rows_per_unit = p2_row_cnt(M) < ny ? p2_row_cnt(M) : ny;
+  if (cs == 8 && rc.e == 16 && p2_col_ok(ny)) t.cols_per_unit = p2_col_cnt(ny);
   // small path: whole half spectrum resident in shared memory
   int sr = ny < kMaxThreads / tr ? ny : kMaxThreads / tr;
   int sc = (M + 1) < kMaxThreads / tcl ? (M + 1) : kMaxThreads / tcl;
@@ -215,6 +227,18 @@ int fs_size_supported(int n) { return size_supported(n) ? 1 : 0; }
 int fs_radix_plan(int L, int e, int *out, int cap) { return radix_plan(L, e, out, cap); }
 
 uint64_t fs_kernel_launches(void) { return g_launches.load(); }
+
+fs_status fs_device_status(int *code) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_fs_dev_error, sizeof(int));
+  if (e == cudaSuccess && v) {
+    const int zero = 0;
+    e = cudaMemcpyToSymbol(g_fs_dev_error, &zero, sizeof(int));
+  }
+  if (e != cudaSuccess) return cuda_error(e, "fs_device_status");
+  if (code) *code = v;
+  return v ? set_error(FS_ERR_TIMEOUT, "a bounded device wait expired") : FS_OK;
+}
 
 fs_status fs_plan_create(int nx, int ny, double lx, double ly, int dtype, fs_plan *out) {
   if (!out) return set_error(FS_ERR_ARG, "fs_plan_create: out is NULL");

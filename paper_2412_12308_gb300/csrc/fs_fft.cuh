@@ -181,7 +181,47 @@ struct XLayout {
   int sidx;
 };
 __device__ __forceinline__ int padi(int p) { return p + (p >> 4); }
-__host__ __device__ inline int padded_len(int n) { return n + (n >> 4) + 1; }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
+
+// Twiddles w^r (r = 1..R-1) for one butterfly, w = tw[step]: the powers
+// w, w^2, w^4, w^8 are read from the FP64-generated table (each rounded once)
+// and the others formed by at most three complex products.
+template <typename T, int R>
+__device__ __forceinline__ void apply_twiddles(cx<T> *b, const cx<T> *__restrict__ tw, int step) {
+  const cx<T> w1 = tw[step];
+  if constexpr (R == 2) {
+    b[1] = cmul(b[1], w1);
+  } else {
+    const cx<T> w2 = tw[2 * step];
+    b[1] = cmul(b[1], w1);
+    b[2] = cmul(b[2], w2);
+    if constexpr (R >= 4) {
+      const cx<T> w3 = cmul(w2, w1);
+      b[3] = cmul(b[3], w3);
+      if constexpr (R >= 5) {
+        const cx<T> w4 = tw[4 * step];
+        b[4] = cmul(b[4], w4);
+        if constexpr (R >= 8) {
+          const cx<T> w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
+          b[5] = cmul(b[5], w5);
+          b[6] = cmul(b[6], w6);
+          b[7] = cmul(b[7], w7);
+          if constexpr (R == 16) {
+            const cx<T> w8 = tw[8 * step];
+            b[8] = cmul(b[8], w8);
+            b[9] = cmul(b[9], cmul(w8, w1));
+            b[10] = cmul(b[10], cmul(w8, w2));
+            b[11] = cmul(b[11], cmul(w8, w3));
+            b[12] = cmul(b[12], cmul(w8, w4));
+            b[13] = cmul(b[13], cmul(w8, w5));
+            b[14] = cmul(b[14], cmul(w8, w6));
+            b[15] = cmul(b[15], cmul(w8, w7));
+          }
+        }
+      }
+    }
+  }
+}
 
 // One Stockham stage of radix R on the register tile.  Butterfly j = t + q*Tseg
 // reads (already in registers, canonical slots q + r*E/R) elements j + r*L/R,
@@ -202,9 +242,7 @@ __device__ __forceinline__ void stage_compute(cx<T> (&v)[E], int t, int Tseg, in
       for (int r = 0; r < R; ++r) b[r] = v[q + r * Q];
       if (Ns > 1) {
         const int k = j % Ns;
-        const int step = twmul * k * (L / (Ns * R));
-#pragma unroll
-        for (int r = 1; r < R; ++r) b[r] = cmul(b[r], tw[step * r]);
+        apply_twiddles<T, R>(b, tw, twmul * k * (L / (Ns * R)));
       }
       dftR<R, false>(b);
 #pragma unroll
@@ -275,6 +313,127 @@ __device__ __forceinline__ void fft_run(cx<T> (&v)[E], cx<T> *sm, XLayout lay, b
       __syncthreads();
     }
     Ns *= R;
+  }
+}
+
+// ------------------------------------------------------------ compile-time engine
+// For power-of-two lengths L and tiles E the stage radices, the running
+// product Ns and every index stride are compile-time constants, so the shared
+// memory addresses reduce to a per-thread base plus immediate offsets.  Same
+// stage sequence and arithmetic as fft_run (largest radix dividing E first).
+namespace ct {
+constexpr int first_radix(int E) { return E % 16 == 0 ? 16 : (E % 8 == 0 ? 8 : (E % 4 == 0 ? 4 : 2)); }
+constexpr int pick(int rem, int E) {
+  int r = first_radix(E);
+  while (rem % r) r >>= 1;
+  return r;
+}
+constexpr int nstages(int L, int E) {
+  int n = 0;
+  for (int rem = L; rem > 1; rem /= pick(rem, E)) ++n;
+  return n;
+}
+constexpr int radix(int L, int E, int st) {
+  int rem = L;
+  for (int i = 0; i < st; ++i) rem /= pick(rem, E);
+  return pick(rem, E);
+}
+constexpr int ns(int L, int E, int st) {
+  int rem = L, p = 1;
+  for (int i = 0; i < st; ++i) {
+    const int r = pick(rem, E);
+    rem /= r;
+    p *= r;
+  }
+  return p;
+}
+constexpr bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+}  // namespace ct
+
+template <typename T, int E, int L, int SIDX, int TWMUL, int ST>
+__device__ __forceinline__ void fft_ct_from(cx<T> (&v)[E], cx<T> *sm, int base, bool active, int t,
+                                            const cx<T> *__restrict__ tw) {
+  constexpr int NST = ct::nstages(L, E);
+  if constexpr (ST < NST) {
+    constexpr int R = ct::radix(L, E, ST);
+    constexpr int NS = ct::ns(L, E, ST);
+    constexpr int Tseg = L / E;
+    constexpr int Q = E / R;
+    static_assert(E % R == 0, "radix must divide the tile");
+    if constexpr (ST > 0) {
+      if (active) {
+        const int pb = base + t * SIDX;
+        const int ppb = padi(pb);
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+          // canonical slot s <-> index t + Tseg*s
+          const int off = Tseg * SIDX * s;
+          v[s] = sm[(off % 16 == 0) ? ppb + off + off / 16 : padi(pb + off)];
+        }
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int j = t + q * Tseg;
+        cx<T> b[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) b[r] = v[q + r * Q];
+        if constexpr (NS > 1) {
+          const int k = j & (NS - 1);
+          apply_twiddles<T, R>(b, tw, TWMUL * (L / (NS * R)) * k);
+        }
+        dftR<R, false>(b);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q + r * Q] = b[r];
+      }
+    }
+    if constexpr (ST < NST - 1) {
+      __syncthreads();
+      if (active) {
+        if constexpr (NS <= Tseg) {
+          // Ns divides Tseg: expand(j) = expand(t) + q*Tseg*R
+          const int bt = (t / NS) * (NS * R) + (t & (NS - 1));
+          const int pb = base + bt * SIDX;
+          const int ppb = padi(pb);
+#pragma unroll
+          for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int off = (q * Tseg * R + r * NS) * SIDX;
+              sm[(off % 16 == 0) ? ppb + off + off / 16 : padi(pb + off)] = v[q + r * Q];
+            }
+        } else {
+          // Tseg divides Ns: j < Ns within each q block, expand(j) = const(q) + t
+          const int pb = base + t * SIDX;
+          const int ppb = padi(pb);
+#pragma unroll
+          for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int jq = q * Tseg;
+              const int off = ((jq / NS) * (NS * R) + (jq % NS) + r * NS) * SIDX;
+              sm[(off % 16 == 0) ? ppb + off + off / 16 : padi(pb + off)] = v[q + r * Q];
+            }
+        }
+      }
+      __syncthreads();
+    }
+    fft_ct_from<T, E, L, SIDX, TWMUL, ST + 1>(v, sm, base, active, t, tw);
+  }
+}
+
+// Engine selection: LC > 0 selects the compile-time engine for length LC
+// with exchange stride SIDX; LC == 0 the runtime engine.
+template <typename T, int E, int LC, int SIDX, int TWMUL>
+__device__ __forceinline__ void fft_any(cx<T> (&v)[E], cx<T> *sm, XLayout lay, bool active, int t,
+                                        int Tseg, int L, const RadixPlan &rp,
+                                        const cx<T> *__restrict__ tw) {
+  if constexpr (LC > 0) {
+    static_assert(SIDX > 0 && ct::is_pow2(LC), "compile-time engine: pow2 length, fixed stride");
+    fft_ct_from<T, E, LC, SIDX, TWMUL, 0>(v, sm, lay.base, active, t, tw);
+  } else {
+    fft_run<T, E>(v, sm, lay, active, t, Tseg, L, rp, tw, TWMUL);
   }
 }
 

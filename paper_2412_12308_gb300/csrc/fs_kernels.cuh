@@ -4,11 +4,15 @@
 #pragma once
 #include <atomic>
 
+#include "fs_pow2.h"
 #include "fs_units.cuh"
 
 namespace fs {
 
 extern std::atomic<unsigned long long> g_launches;
+
+// TMA-staged kernels can be switched off (env FS_NO_TMA=1) for comparison.
+bool tma_enabled();
 
 // Optional per-launch event timing (fs_profile_enable); classes as in fsolve.h.
 enum ProfClass { PC_R2C = 0, PC_COL = 1, PC_C2R = 2, PC_FACTOR = 3, PC_SMALL = 4, PC_BATCH = 5, PC_N = 6 };
@@ -188,8 +192,23 @@ struct Launch {
     return round_up32(a > b ? a : b);
   }
   static cudaError_t set_smem(const void *fn, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    // prefer the largest shared-memory carveout so several CTAs fit per SM
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess || bytes <= 48 * 1024) return e;
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
+  // power-of-two FP32 kernels with compile-time lengths, when the plan's tile
+  // shapes are the ones they were compiled for
+  static PassKernel p2_row(const Desc &d, bool c2r) {
+    if (sizeof(T) != 4 || d.rp_row.e != 16 || !p2_row_ok(d.M) || d.rows_per_unit != p2_row_cnt(d.M))
+      return nullptr;
+    return c2r ? p2_c2r_f32(d.M) : p2_r2c_f32(d.M);
+  }
+  static PassKernel p2_col(const Desc &d) {
+    if (sizeof(T) != 4 || d.rp_col.e != 16 || !p2_col_ok(d.ny) || d.cols_per_unit != p2_col_cnt(d.ny))
+      return nullptr;
+    return col_two_fields(d) ? p2_col2_f32(d.ny) : p2_col1_f32(d.ny);
   }
 
   static cudaError_t launch(PassKernel k, int grid, int threads, size_t sm, const Desc &d,
@@ -204,17 +223,41 @@ struct Launch {
   }
   // forward pass over the real field(s): fields = 1 or 2
   static cudaError_t rows(const Desc &d, int fields, cudaStream_t s) {
-    return launch(pass_kernels<T>(d.rp_row.e).r2c, d.n_row_units * fields, row_threads(d),
-                  row_smem(d), d, s, PC_R2C);
+    PassKernel k = p2_row(d, false);
+    if (!k) k = pass_kernels<T>(d.rp_row.e).r2c;
+    return launch(k, d.n_row_units * fields, row_threads(d), row_smem(d), d, s, PC_R2C);
   }
   static cudaError_t cols(const Desc &d, cudaStream_t s) {
-    const PassKernels pk = pass_kernels<T>(d.rp_col.e);
-    return launch(col_two_fields(d) ? pk.col2 : pk.col1, d.n_col_units, col_threads(d),
-                  col_smem(d), d, s, PC_COL);
+    // TMA-staged persistent kernel for single-field FP32 power-of-two columns
+    if (sizeof(T) == 4 && !col_two_fields(d) && p2_col(d) && tma_enabled()) {
+      PassKernel k = p2_col_tma_f32(d.ny);
+      const size_t sm = p2_col_tma_smem(d.ny);
+      cudaError_t e = set_smem((const void *)k, sm);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0, sms = 0, dev = 0;
+      const int threads = d.cols_per_unit * (d.ny / 16);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, sm);
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      int grid = sms * (per_sm > 0 ? per_sm : 1);
+      if (grid > d.n_col_units) grid = d.n_col_units;
+      ProfScope ps(PC_COL, s);
+      k<<<grid, threads, sm, s>>>(d);
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      return cudaGetLastError();
+    }
+    PassKernel k = p2_col(d);
+    if (!k) {
+      const PassKernels pk = pass_kernels<T>(d.rp_col.e);
+      k = col_two_fields(d) ? pk.col2 : pk.col1;
+    }
+    return launch(k, d.n_col_units, col_threads(d), col_smem(d), d, s, PC_COL);
   }
   static cudaError_t c2r(const Desc &d, int fields, cudaStream_t s) {
-    return launch(pass_kernels<T>(d.rp_row.e).c2r, d.n_row_units * fields, row_threads(d),
-                  row_smem(d), d, s, PC_C2R);
+    PassKernel k = p2_row(d, true);
+    if (!k) k = pass_kernels<T>(d.rp_row.e).c2r;
+    return launch(k, d.n_row_units * fields, row_threads(d), row_smem(d), d, s, PC_C2R);
   }
   static cudaError_t factor(const Desc &d, cudaStream_t s) {
     ProfScope ps(PC_FACTOR, s);

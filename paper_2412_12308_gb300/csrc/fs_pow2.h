@@ -1,0 +1,30 @@
+// fs_pow2.h -- pass kernels specialised at compile time for power-of-two
+// lengths (FP32, 16-element register tiles).  Each kernel inlines one unit
+// with the transform length and the rows/columns per CTA fixed, so the FFT
+// engine's strides and stage structure are constants.
+#pragma once
+#include "fs_desc.h"
+
+namespace fs {
+
+typedef void (*PassKernel)(const Desc);
+
+// Column pass: 256 threads per CTA (512 for length 8192).
+constexpr int p2_col_cnt(int L) { return (L / 16) >= 256 ? 1 : 256 / (L / 16); }
+constexpr bool p2_col_ok(int L) { return L >= 128 && L <= 8192 && (L & (L - 1)) == 0; }
+// Row passes (length M = nx/2): up to 16 rows and 512 threads per CTA.
+constexpr int p2_row_cnt(int M) {
+  return (M / 16) >= 256 ? 2 : ((M / 16) * 16 <= 512 ? 16 : 512 / (M / 16));
+}
+constexpr bool p2_row_ok(int M) { return M >= 128 && M <= 4096 && (M & (M - 1)) == 0; }
+
+// Kernel lookup (nullptr when not specialised).
+PassKernel p2_r2c_f32(int M);
+PassKernel p2_c2r_f32(int M);
+PassKernel p2_col1_f32(int L);
+PassKernel p2_col2_f32(int L);
+// TMA-staged persistent column kernel (single field) and its shared memory.
+PassKernel p2_col_tma_f32(int L);
+size_t p2_col_tma_smem(int L);
+
+}  // namespace fs

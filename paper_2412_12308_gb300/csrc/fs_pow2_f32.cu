@@ -1,0 +1,229 @@
+// FP32 pass kernels specialised for power-of-two lengths (see fs_pow2.h).
+#include "fs_pow2.h"
+#include "fs_tma.cuh"
+#include "fs_units.cuh"
+
+namespace fs {
+
+namespace {
+template <int THREADS>
+constexpr int min_blocks() {
+  return THREADS >= 512 ? 2 : (THREADS >= 256 ? 3 : 6);
+}
+}  // namespace
+
+template <int M>
+struct RowK {
+  static constexpr int CC = p2_row_cnt(M);
+  static constexpr int THREADS = CC * (M / 16);
+};
+template <int L>
+struct ColK {
+  static constexpr int CC = p2_col_cnt(L);
+  static constexpr int THREADS = CC * (L / 16);
+};
+
+template <int M>
+__global__ void __launch_bounds__(RowK<M>::THREADS, min_blocks<RowK<M>::THREADS>()) k_r2c_p2(const Desc d) {
+  extern __shared__ __align__(16) unsigned char fs_smem[];
+  int unit = blockIdx.x;
+  const float *in = reinterpret_cast<const float *>(d.in_u);
+  cx<float> *spec = reinterpret_cast<cx<float> *>(d.work_u);
+  if (unit >= d.n_row_units) {
+    unit -= d.n_row_units;
+    in = reinterpret_cast<const float *>(d.in_v);
+    spec = reinterpret_cast<cx<float> *>(d.work_v);
+  }
+  unit_row_r2c_t<float, 16, M, RowK<M>::CC>(d, unit, RowK<M>::CC, reinterpret_cast<cx<float> *>(fs_smem), in,
+                                           spec);
+}
+
+template <int M>
+__global__ void __launch_bounds__(RowK<M>::THREADS, min_blocks<RowK<M>::THREADS>()) k_c2r_p2(const Desc d) {
+  extern __shared__ __align__(16) unsigned char fs_smem[];
+  int unit = blockIdx.x;
+  const cx<float> *spec = reinterpret_cast<const cx<float> *>(d.work_u);
+  float *out = reinterpret_cast<float *>(d.out_u);
+  if (unit >= d.n_row_units) {
+    unit -= d.n_row_units;
+    spec = reinterpret_cast<const cx<float> *>(d.work_v);
+    out = reinterpret_cast<float *>(d.out_v);
+  }
+  unit_row_c2r_t<float, 16, M, RowK<M>::CC>(d, unit, RowK<M>::CC, reinterpret_cast<cx<float> *>(fs_smem), spec,
+                                           out, false);
+}
+
+template <int L, bool TWO>
+__global__ void __launch_bounds__(ColK<L>::THREADS, min_blocks<ColK<L>::THREADS>()) k_col_p2(const Desc d) {
+  extern __shared__ __align__(16) unsigned char fs_smem[];
+  unit_col_t<float, 16, TWO, L, ColK<L>::CC>(d, blockIdx.x, ColK<L>::CC, reinterpret_cast<cx<float> *>(fs_smem),
+                                             reinterpret_cast<cx<float> *>(d.work_u),
+                                             reinterpret_cast<cx<float> *>(d.work_v), false);
+}
+
+// ---------------------------------------------------------------- TMA column pass
+// Persistent CTAs walk column groups a = blockIdx.x*CC, += gridDim.x*CC.  The
+// CC columns of a group are one contiguous run of the x-frequency-major
+// spectrum, so a single bulk copy (cp.async.bulk, completion on an mbarrier)
+// stages the NEXT group into shared memory while the current group is
+// transformed; the current buffer doubles as the FFT exchange area.  Single
+// field only (the two-field wave variants use k_col_p2).
+template <int L, int CC>
+__device__ __forceinline__ void col_tma_body(const Desc &d, cx<float> *buf0, cx<float> *buf1, uint64_t *bars,
+                                             int *s_abort) {
+  constexpr int E = 16, Tseg = L / E;
+  const int tid = threadIdx.x;
+  const int rho = tid / Tseg, t = tid - rho * Tseg;
+  const int ncols = d.M + 1;
+  const bool adv = (d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV);
+  const cx<float> *src = reinterpret_cast<const cx<float> *>(adv ? d.st_u : d.work_u);
+  cx<float> *dst = reinterpret_cast<cx<float> *>(d.work_u);
+  const cx<float> *tw = reinterpret_cast<const cx<float> *>(d.tw_y);
+  const int g0 = blockIdx.x * CC, gstride = gridDim.x * CC;
+  auto issue = [&](cx<float> *b, uint64_t *bar, int g) {
+    const int nc = min(CC, ncols - g);
+    const uint32_t bytes = (uint32_t)(nc * L * sizeof(cx<float>));
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(b, src + (size_t)g * L, bytes, bar);
+  };
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+    *s_abort = 0;
+    if (g0 < ncols) issue(buf0, &bars[0], g0);
+  }
+  __syncthreads();
+  int i = 0;
+  for (int g = g0; g < ncols; g += gstride, ++i) {
+    cx<float> *cur = (i & 1) ? buf1 : buf0;
+    cx<float> *nxt = (i & 1) ? buf0 : buf1;
+    if (tid == 0 && g + gstride < ncols) {
+      fence_proxy_async_smem();
+      issue(nxt, &bars[(i + 1) & 1], g + gstride);
+    }
+    // every thread observes the copy's completion itself (bounded)
+    if (!mbar_wait_bounded(&bars[i & 1], (uint32_t)((i >> 1) & 1), kTmaWaitNs)) {
+      atomicExch(&g_fs_dev_error, FS_DEV_ERR_TMA_TIMEOUT);
+      *s_abort = 1;
+    }
+    __syncthreads();
+    if (*s_abort) {
+      // let the copy still in flight land before the CTA exits
+      if (tid == 0 && g + gstride < ncols)
+        mbar_wait_bounded(&bars[(i + 1) & 1], (uint32_t)(((i + 1) >> 1) & 1), kTmaWaitNs);
+      break;
+    }
+    const int a = g + rho;
+    const bool active = a < ncols;
+    cx<float> u[E];
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) u[s] = cur[rho * L + t + Tseg * s];
+    } else {
+#pragma unroll
+      for (int s = 0; s < E; ++s) u[s] = zero_cx<float>();
+    }
+    const XLayout lay{rho * L, 1};
+    if (!adv) fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
+    if (d.op == OP_FORWARD) {
+      if (active) {
+        cx<float> *ou = reinterpret_cast<cx<float> *>(d.st_out_u) + (size_t)a * L;
+#pragma unroll
+        for (int s = 0; s < E; ++s) ou[t + Tseg * s] = u[s];
+      }
+    } else {
+      if (active) col_op_single<float, E>(d, op_ctx<float>(d, a), t, Tseg, u);
+      __syncthreads();
+      fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
+      if (active) {
+        cx<float> *o = dst + (size_t)a * L;
+#pragma unroll
+        for (int s = 0; s < E; ++s) o[t + Tseg * s] = conj(u[s]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int L>
+struct ColT {
+  static constexpr int CC = p2_col_cnt(L);
+  static constexpr int THREADS = CC * (L / 16);
+  static constexpr int PLEN = (padded_len(CC * L) + 1) & ~1;  // even: keeps buffer 1 16-byte aligned
+};
+
+template <int L>
+__global__ void __launch_bounds__(ColT<L>::THREADS, min_blocks<ColT<L>::THREADS>()) k_col_tma(const Desc d) {
+  extern __shared__ __align__(128) unsigned char fs_smem[];
+  __shared__ uint64_t bars[2];
+  __shared__ int s_abort;
+  cx<float> *b0 = reinterpret_cast<cx<float> *>(fs_smem);
+  col_tma_body<L, ColT<L>::CC>(d, b0, b0 + ColT<L>::PLEN, bars, &s_abort);
+}
+
+#define FS_P2_ROWS(X) X(128) X(256) X(512) X(1024) X(2048) X(4096)
+#define FS_P2_COLS(X) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+
+PassKernel p2_r2c_f32(int M) {
+  switch (M) {
+#define C(m) \
+  case m:    \
+    return k_r2c_p2<m>;
+    FS_P2_ROWS(C)
+#undef C
+    default:
+      return nullptr;
+  }
+}
+PassKernel p2_c2r_f32(int M) {
+  switch (M) {
+#define C(m) \
+  case m:    \
+    return k_c2r_p2<m>;
+    FS_P2_ROWS(C)
+#undef C
+    default:
+      return nullptr;
+  }
+}
+PassKernel p2_col1_f32(int L) {
+  switch (L) {
+#define C(l) \
+  case l:    \
+    return k_col_p2<l, false>;
+    FS_P2_COLS(C)
+#undef C
+    default:
+      return nullptr;
+  }
+}
+PassKernel p2_col_tma_f32(int L) {
+  switch (L) {
+#define C(l) \
+  case l:    \
+    return k_col_tma<l>;
+    FS_P2_COLS(C)
+#undef C
+    default:
+      return nullptr;
+  }
+}
+size_t p2_col_tma_smem(int L) {
+  const int cc = p2_col_cnt(L);
+  return 2 * (size_t)((padded_len(cc * L) + 1) & ~1) * 8;
+}
+
+PassKernel p2_col2_f32(int L) {
+  switch (L) {
+#define C(l) \
+  case l:    \
+    return k_col_p2<l, true>;
+    FS_P2_COLS(C)
+#undef C
+    default:
+      return nullptr;
+  }
+}
+
+}  // namespace fs

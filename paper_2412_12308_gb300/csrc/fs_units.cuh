@@ -16,6 +16,7 @@
 // and read runs of `rows_per_unit` consecutive y values per frequency.
 #pragma once
 #include "fs_ops.cuh"
+#include "fs_pow2.h"
 
 namespace fs {
 
@@ -54,10 +55,12 @@ __device__ __forceinline__ cx<T> zero_cx() {
 // z_m = x_{2m} + i x_{2m+1} for m = t + Tseg*s.  After the length-M complex
 // transform Z, X_a = (Z_a + conj Z_{M-a})/2 + w^a (Z_a - conj Z_{M-a})/(2i),
 // w = e^{-2 pi i/nx}; X_0 and X_M are real.
-template <typename T, int E>
-__device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt, cx<T> *sm,
-                                          const T *__restrict__ in, cx<T> *spec) {
-  const int M = d.M, ny = d.ny, Tseg = M / E;
+// MC, CC: compile-time row length M and rows per tile (0 = read from d / cnt_rt).
+template <typename T, int E, int MC = 0, int CC = 0>
+__device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt_rt, cx<T> *sm,
+                                               const T *__restrict__ in, cx<T> *spec) {
+  const int M = MC ? MC : d.M, ny = d.ny, Tseg = M / E;
+  const int cnt = CC ? CC : cnt_rt;
   const int tid = threadIdx.x;
   const int t = tid / cnt, rho = tid - t * cnt;
   const int y = unit * cnt + rho;
@@ -73,7 +76,7 @@ __device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt,
 #pragma unroll
     for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();
   }
-  fft_run<T, E>(v, sm, lay, active, t, Tseg, M, d.rp_row, tw, 2);
+  fft_any<T, E, MC, CC, 2>(v, sm, lay, active, t, Tseg, M, d.rp_row, tw);
   __syncthreads();
   if (active) {
 #pragma unroll
@@ -106,10 +109,11 @@ __device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt,
 // the inverse length-M transform of F + iG gives x_{2m} + i x_{2m+1}.
 // The imaginary parts of X_0 and X_M are ignored (they are zero for a real
 // result).  No scaling here: 1/(nx ny) is folded into the spectral multiplier.
-template <typename T, int E>
-__device__ __forceinline__ void unit_row_c2r_t(const Desc &d, int unit, int cnt, cx<T> *sm,
-                                          const cx<T> *spec, T *out, bool sh) {
-  const int M = d.M, ny = d.ny, Tseg = M / E;
+template <typename T, int E, int MC = 0, int CC = 0>
+__device__ __forceinline__ void unit_row_c2r_t(const Desc &d, int unit, int cnt_rt, cx<T> *sm,
+                                               const cx<T> *spec, T *out, bool sh) {
+  const int M = MC ? MC : d.M, ny = d.ny, Tseg = M / E;
+  const int cnt = CC ? CC : cnt_rt;
   const int tid = threadIdx.x;
   const int t = tid / cnt, rho = tid - t * cnt;
   const int y = unit * cnt + rho;
@@ -149,7 +153,7 @@ __device__ __forceinline__ void unit_row_c2r_t(const Desc &d, int unit, int cnt,
       v[s] = mk<T>(f.x - g.y, -(f.y + g.x));
     }
   }
-  fft_run<T, E>(v, sm, lay, active, t, Tseg, M, d.rp_row, tw, 2);
+  fft_any<T, E, MC, CC, 2>(v, sm, lay, active, t, Tseg, M, d.rp_row, tw);
   conj_tile(v);
   if (active) {
     cx<T> *row = reinterpret_cast<cx<T> *>(out + (size_t)y * d.nx);
@@ -166,6 +170,24 @@ __device__ __forceinline__ void unit_row_c2r_t(const Desc &d, int unit, int cnt,
 //   OP_FORWARD   : load work, forward y-DFT, store the kept spectrum
 //   advance ops  : load kept spectra, multiply, inverse y-DFT, store work
 // `wu`, `wv` are the work spectra (global, or shared in the small path).
+// Single-field spectral operator on a column's register tile (frequency
+// b = t + Tseg*s), results conjugated for the inverse-by-conjugation step.
+template <typename T, int E>
+__device__ __forceinline__ void col_op_single(const Desc &d, const OpCtx<T> &o, int t, int Tseg,
+                                              cx<T> (&u)[E]) {
+  const int op = d.op;
+  if (op == OP_POISSON) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) u[s] = conj(poisson_mult(o, d, t + Tseg * s) * u[s]);
+  } else if (op == OP_DIFFUSION || op == OP_DIFF_ADV) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) u[s] = conj(diff_mult(o, d, t + Tseg * s) * u[s]);
+  } else {  // wave, zero initial velocity
+#pragma unroll
+    for (int s = 0; s < E; ++s) u[s] = conj(wave_mult(o, d, t + Tseg * s).cu * u[s]);
+  }
+}
+
 // TWO: a second field (initial velocity in, or velocity out) is carried;
 // the single-field variant holds one register tile only.
 __host__ __device__ inline bool col_two_fields(const Desc &d) {
@@ -175,10 +197,12 @@ __host__ __device__ inline bool col_two_fields(const Desc &d) {
          (d.op == OP_WAVE_ADV && want_v);
 }
 
-template <typename T, int E, bool TWO>
-__device__ __forceinline__ void unit_col_t(const Desc &d, int unit, int cnt, cx<T> *sm, cx<T> *wu,
+// LC, CC: compile-time column length and columns per unit (0 = from d / cnt_rt).
+template <typename T, int E, bool TWO, int LC = 0, int CC = 0>
+__device__ __forceinline__ void unit_col_t(const Desc &d, int unit, int cnt_rt, cx<T> *sm, cx<T> *wu,
                                            cx<T> *wv, bool sh) {
-  const int L = d.ny, M = d.M, Tseg = L / E;
+  const int L = LC ? LC : d.ny, M = d.M, Tseg = L / E;
+  const int cnt = CC ? CC : cnt_rt;
   const int tid = threadIdx.x;
   const int rho = tid / Tseg, t = tid - rho * Tseg;
   const int a = unit * cnt + rho;
@@ -221,11 +245,11 @@ __device__ __forceinline__ void unit_col_t(const Desc &d, int unit, int cnt, cx<
         __syncthreads();
         swap_tile(u, w);
       }
-      fft_run<T, E>(u, sm, lay, active, t, Tseg, L, d.rp_col, tw, 1);
+      fft_any<T, E, LC, 1, 1>(u, sm, lay, active, t, Tseg, L, d.rp_col, tw);
       if (f) swap_tile(u, w);
     }
   } else {
-    if (!adv) fft_run<T, E>(u, sm, lay, active, t, Tseg, L, d.rp_col, tw, 1);
+    if (!adv) fft_any<T, E, LC, 1, 1>(u, sm, lay, active, t, Tseg, L, d.rp_col, tw);
   }
   if (op == OP_FORWARD) {
     if (active) {
@@ -247,12 +271,8 @@ __device__ __forceinline__ void unit_col_t(const Desc &d, int unit, int cnt, cx<
   // inverse transform by conjugation
   if (active) {
     const OpCtx<T> o = op_ctx<T>(d, a);
-    if (op == OP_POISSON) {
-#pragma unroll
-      for (int s = 0; s < E; ++s) u[s] = conj(poisson_mult(o, d, t + Tseg * s) * u[s]);
-    } else if (op == OP_DIFFUSION || op == OP_DIFF_ADV) {
-#pragma unroll
-      for (int s = 0; s < E; ++s) u[s] = conj(diff_mult(o, d, t + Tseg * s) * u[s]);
+    if (op == OP_POISSON || op == OP_DIFFUSION || op == OP_DIFF_ADV || !TWO) {
+      col_op_single<T, E>(d, o, t, Tseg, u);
     } else if constexpr (TWO) {  // wave carrying a velocity field
 #pragma unroll
       for (int s = 0; s < E; ++s) {
@@ -261,9 +281,6 @@ __device__ __forceinline__ void unit_col_t(const Desc &d, int unit, int cnt, cx<
         u[s] = conj(f.cu * u0 + f.su * v0);
         w[s] = conj(f.sv * u0 + f.cu * v0);
       }
-    } else {  // wave, zero initial velocity, u only
-#pragma unroll
-      for (int s = 0; s < E; ++s) u[s] = conj(wave_mult(o, d, t + Tseg * s).cu * u[s]);
     }
   }
   // ---- inverse y transforms
@@ -274,7 +291,7 @@ __device__ __forceinline__ void unit_col_t(const Desc &d, int unit, int cnt, cx<
     if constexpr (TWO) {
       if (f) swap_tile(u, w);
     }
-    fft_run<T, E>(u, sm, lay, active, t, Tseg, L, d.rp_col, tw, 1);
+    fft_any<T, E, LC, 1, 1>(u, sm, lay, active, t, Tseg, L, d.rp_col, tw);
     if (active) {
       cx<T> *dst = (f ? wv : wu) + cofs;
 #pragma unroll
@@ -444,7 +461,6 @@ FS_FOR_EACH_E_double(FS_UNIT_DECL)
   }
 
 // Host-side kernel lookup by register tile.
-typedef void (*PassKernel)(const Desc);
 struct PassKernels {
   PassKernel r2c, c2r, col1, col2;
 };

@@ -65,6 +65,7 @@ _SIGS = {
     "fs_size_supported": (ctypes.c_int, [ctypes.c_int]),
     "fs_radix_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "fs_kernel_launches": (ctypes.c_uint64, []),
+    "fs_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "fs_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "fs_profile_report": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_int]),
@@ -243,6 +244,14 @@ def fs_radix_plan(L, e):
     buf = (ctypes.c_int * 8)()
     n = _lib.fs_radix_plan(int(L), int(e), buf, 8)
     return [buf[i] for i in range(n)]
+
+
+def fs_device_status():
+    """Device error code of the kernels' bounded waits (0 = none); cleared on read."""
+    load()
+    code = ctypes.c_int()
+    _lib.fs_device_status(ctypes.byref(code))
+    return code.value
 
 
 def fs_kernel_launches():
