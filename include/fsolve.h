@@ -150,6 +150,11 @@ typedef struct fs_request {
   void *out_u;
   void *out_v;
   double D, c, t;
+  /* serving only (ignored by fs_batch_submit): */
+  int keep;        /* diffusion / zero-velocity wave solve: keep the forward
+                      spectrum for this many follow-up requests */
+  uint64_t parent; /* advance op: ticket of the request whose kept spectrum
+                      to advance (instead of `state`) */
 } fs_request;
 
 /* fs_batch_submit: run n independent requests (any mix of sizes, operators
@@ -171,6 +176,37 @@ fs_status fs_batch_submit(const fs_request *reqs, int n, uint64_t *ticket_out, f
 /* Block until batch `ticket` finished (bounded by timeout_us; <0 = no bound);
  * returns the batch's device status (FS_OK or FS_ERR_TIMEOUT) or a wait error. */
 fs_status fs_batch_wait(uint64_t ticket, int timeout_us);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of solve and advance requests (Sec. III solves served
+ * as a stream; the kept spectra realise the paper's observation that the IVP
+ * in Fourier space is fixed by f-hat, so later times need only the inverse
+ * transform).  A server thread forms batches from the queue in arrival order
+ * whenever one of `slots` in-flight batches (each on its own stream) is free;
+ * a request is admitted when its workspace plus the spectrum it keeps fits the
+ * HBM budget next to everything in flight and kept; follow-ups wait until
+ * their parent's spectrum is on the device.  One server per process.
+ * fs_serve_start: budget (bytes, reserved on the current device), slots >= 2,
+ *   max requests per batch.
+ * fs_serve_enqueue: copy a request into the queue; *ticket_out names it.
+ *   FS_ERR_BUDGET if it can never fit, FS_ERR_BUSY if the queue is full.
+ * fs_serve_replay: open-loop driver -- enqueue reqs[i] at arrival_s[i]
+ *   seconds after the call (blocking until the last is enqueued); a
+ *   follow-up's `parent` is given as (index of its parent in reqs) + 1.
+ * fs_serve_poll: harvest up to `cap` finished tickets, waiting at most
+ *   timeout_us (< 0: unbounded) for one; *n_done receives the count.
+ * fs_serve_latency: enqueue -> observed completion, microseconds.
+ * fs_serve_stats: batches, completed, max in flight, batches launched while
+ *   another was in flight, peak bytes used, bytes used, queued, kept.
+ * fs_serve_stop: drain the queue, wait for in-flight work, release memory. */
+fs_status fs_serve_start(size_t hbm_budget_bytes, int slots, int max_batch);
+fs_status fs_serve_enqueue(const fs_request *req, uint64_t *ticket_out);
+fs_status fs_serve_replay(const fs_request *reqs, const double *arrival_s, int n, uint64_t *tickets_out);
+fs_status fs_serve_poll(uint64_t *done_tickets, int cap, int *n_done, int timeout_us);
+fs_status fs_serve_latency(uint64_t ticket, double *latency_us);
+fs_status fs_serve_stats(uint64_t *out, int cap);
+fs_status fs_serve_stop(void);
+
 
 /* ---------------------------------------------------------------- no allocation
  * fs_poisson_solve_static: the same FP32 Poisson solve as fs_poisson_solve,

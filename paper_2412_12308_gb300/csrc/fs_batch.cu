@@ -97,7 +97,7 @@ void drop_graph(Slot *s) {
 }  // namespace
 
 // ---------------------------------------------------------------- planning
-fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp) {
+fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *const *keep_out) {
   bp->descs.clear();
   bp->units.clear();
   bp->arena_bytes = 0;
@@ -169,6 +169,11 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp) {
         break;
       default:
         return set_error(FS_ERR_ARG, "fs_batch_submit: unknown op");
+    }
+    if (keep_out && keep_out[i]) {
+      if (d.op != OP_DIFFUSION && !(d.op == OP_WAVE && !(d.flags & F_HAS_V0)))
+        return set_error(FS_ERR_ARG, "keep: only diffusion and zero-velocity wave solves keep spectra");
+      d.st_out_u = keep_out[i];
     }
     const bool diff = d.op == OP_DIFFUSION || d.op == OP_DIFF_ADV;
     const int nspec = small_nspec(d);
@@ -286,11 +291,19 @@ static size_t finish_descs(BatchPlan *bp, char *arena) {
 
 }  // namespace fs
 
-using namespace fs;
+namespace fs {
 
-static fs_status submit_impl(const fs_request *reqs, int n, uint64_t *ticket_out, cudaStream_t stream) {
+fs_status request_workspace(const fs_request &r, size_t *bytes) {
   BatchPlan bp;
-  fs_status st = plan_requests(reqs, n, &bp);
+  const fs_status st = plan_requests(&r, 1, &bp);
+  *bytes = st == FS_OK ? bp.arena_bytes : 0;
+  return st;
+}
+
+fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep_out, uint64_t *ticket_out,
+                                cudaStream_t stream, char *ext_arena, size_t ext_bytes) {
+  BatchPlan bp;
+  fs_status st = plan_requests(reqs, n, &bp, keep_out);
   if (st != FS_OK) return st;
   const unsigned long long wait_ns = (unsigned long long)env_ll("FS_BATCH_WAIT_NS", 2000000000LL);
   const bool inject = env_ll("FS_BATCH_INJECT_STALL", 0) != 0;
@@ -335,7 +348,9 @@ static fs_status submit_impl(const fs_request *reqs, int n, uint64_t *ticket_out
   const size_t cu = s->cap_units;
   if (e == cudaSuccess) e = grow(&s->d_units, &s->h_units, s->cap_units, nu);
   if (e == cudaSuccess && s->cap_units != cu) drop_graph(s);
-  if (e == cudaSuccess && bp.arena_bytes > s->cap_arena) {
+  if (ext_arena && ext_bytes < bp.arena_bytes)
+    return set_error(FS_ERR_ARG, "batch: external arena smaller than the batch workspace");
+  if (e == cudaSuccess && !ext_arena && bp.arena_bytes > s->cap_arena) {
     cudaFree(s->d_arena);
     s->d_arena = nullptr;
     s->cap_arena = 0;
@@ -345,8 +360,8 @@ static fs_status submit_impl(const fs_request *reqs, int n, uint64_t *ticket_out
   if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: buffer allocation");
 
   const int dtype = bp.dtype;
-  const size_t smem = dtype == FS_F64 ? finish_descs<double>(&bp, s->d_arena)
-                                      : finish_descs<float>(&bp, s->d_arena);
+  char *arena = ext_arena ? ext_arena : s->d_arena;
+  const size_t smem = dtype == FS_F64 ? finish_descs<double>(&bp, arena) : finish_descs<float>(&bp, arena);
   if (smem > kMaxDynSmem) return set_error(FS_ERR_SIZE, "fs_batch_submit: unit shared memory too large");
   if (inject) {
     // test hook: make the first three-pass problem's column units wait for a
@@ -415,10 +430,14 @@ static fs_status submit_impl(const fs_request *reqs, int n, uint64_t *ticket_out
   return FS_OK;
 }
 
+}  // namespace fs
+
+using namespace fs;
+
 extern "C" fs_status fs_batch_submit(const fs_request *reqs, int n, uint64_t *ticket_out, fs_stream stream) {
   if (ticket_out) *ticket_out = 0;
   if (!reqs || n <= 0) return set_error(FS_ERR_ARG, "fs_batch_submit: empty batch");
-  return submit_impl(reqs, n, ticket_out, reinterpret_cast<cudaStream_t>(stream));
+  return batch_submit_internal(reqs, n, nullptr, ticket_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" fs_status fs_batch_wait(uint64_t ticket, int timeout_us) {

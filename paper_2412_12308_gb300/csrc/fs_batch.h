@@ -19,6 +19,17 @@ struct BatchPlan {
 };
 
 // Validate requests and build descriptors + work table (no device work).
-fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp);
+// keep_out[i] (optional): device buffer that receives request i's forward
+// half spectrum (diffusion / wave solves with zero initial velocity).
+fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *const *keep_out = nullptr);
+
+// Submit a planned batch on `stream` (see fs_batch_submit).
+// ext_arena (optional, >= the batch's workspace bytes) replaces the slot's own
+// arena; *ws_bytes_out (optional) receives the batch's workspace bytes.
+fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep_out, uint64_t *ticket_out,
+                                cudaStream_t stream, char *ext_arena = nullptr, size_t ext_bytes = 0);
+
+// Workspace bytes one request needs in a batch arena (validates it).
+fs_status request_workspace(const fs_request &r, size_t *bytes);
 
 }  // namespace fs

@@ -126,13 +126,12 @@ __device__ __forceinline__ void col_tma_body(const Desc &d, cx<float> *buf0, cx<
     }
     const XLayout lay{rho * L, 1};
     if (!adv) fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
-    if (d.op == OP_FORWARD) {
-      if (active) {
-        cx<float> *ou = reinterpret_cast<cx<float> *>(d.st_out_u) + (size_t)a * L;
+    if (!adv && d.st_out_u && active) {  // keep the forward spectrum
+      cx<float> *ou = reinterpret_cast<cx<float> *>(d.st_out_u) + (size_t)a * L;
 #pragma unroll
-        for (int s = 0; s < E; ++s) ou[t + Tseg * s] = u[s];
-      }
-    } else {
+      for (int s = 0; s < E; ++s) ou[t + Tseg * s] = u[s];
+    }
+    if (d.op != OP_FORWARD) {
       if (active) col_op_single<float, E>(d, op_ctx<float>(d, a), t, Tseg, u);
       __syncthreads();
       fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);

@@ -251,19 +251,23 @@ __device__ __forceinline__ void unit_col_t(const Desc &d, int unit, int cnt_rt, 
   } else {
     if (!adv) fft_any<T, E, LC, 1, 1>(u, sm, lay, active, t, Tseg, L, d.rp_col, tw);
   }
-  if (op == OP_FORWARD) {
+  // keep the forward spectrum (state creation, or a solve that keeps its
+  // spectrum for later advances)
+  if (!adv && d.st_out_u) {
     if (active) {
       cx<T> *ou = reinterpret_cast<cx<T> *>(d.st_out_u) + cofs;
 #pragma unroll
       for (int s = 0; s < E; ++s) ou[t + Tseg * s] = u[s];
       if constexpr (TWO) {
-        if (has_v) {
+        if (has_v && d.st_out_v) {
           cx<T> *ov = reinterpret_cast<cx<T> *>(d.st_out_v) + cofs;
 #pragma unroll
           for (int s = 0; s < E; ++s) ov[t + Tseg * s] = w[s];
         }
       }
     }
+  }
+  if (op == OP_FORWARD) {
     __syncthreads();
     return;
   }

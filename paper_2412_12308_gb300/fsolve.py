@@ -37,7 +37,7 @@ class FsRequest(ctypes.Structure):
 
     _fields_ = [("op", ctypes.c_int), ("plan", _vp), ("state", _vp), ("in_u", _vp), ("in_v", _vp),
                 ("out_u", _vp), ("out_v", _vp), ("D", ctypes.c_double), ("c", ctypes.c_double),
-                ("t", ctypes.c_double)]
+                ("t", ctypes.c_double), ("keep", ctypes.c_int), ("parent", ctypes.c_uint64)]
 
 
 # Entry points declared in include/fsolve.h: name -> (restype, argtypes)
@@ -61,6 +61,15 @@ _SIGS = {
     "fs_batch_submit": (ctypes.c_int, [ctypes.POINTER(FsRequest), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                        _vp]),
     "fs_batch_wait": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
+    "fs_serve_start": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
+    "fs_serve_enqueue": (ctypes.c_int, [ctypes.POINTER(FsRequest), ctypes.POINTER(ctypes.c_uint64)]),
+    "fs_serve_replay": (ctypes.c_int, [ctypes.POINTER(FsRequest), ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "fs_serve_poll": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.c_int]),
+    "fs_serve_latency": (ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "fs_serve_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
+    "fs_serve_stop": (ctypes.c_int, []),
     "fs_last_error": (ctypes.c_char_p, []),
     "fs_size_supported": (ctypes.c_int, [ctypes.c_int]),
     "fs_radix_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -205,13 +214,15 @@ def fs_wave_advance(state, c, t, u_out, v_out=None, stream=None):
            "fs_wave_advance")
 
 
-def fs_request(op, plan=None, state=None, in_u=None, in_v=None, out_u=None, out_v=None, D=0.0, c=0.0, t=0.0):
-    """Marshal one batch request (tensors -> device pointers)."""
+def fs_request(op, plan=None, state=None, in_u=None, in_v=None, out_u=None, out_v=None, D=0.0, c=0.0, t=0.0,
+               keep=0, parent=0):
+    """Marshal one batch / serving request (tensors -> device pointers)."""
 
     def p(x):
         return None if x is None else (x if isinstance(x, int) else x.data_ptr())
 
-    return FsRequest(int(op), plan, state, p(in_u), p(in_v), p(out_u), p(out_v), float(D), float(c), float(t))
+    return FsRequest(int(op), plan, state, p(in_u), p(in_v), p(out_u), p(out_v), float(D), float(c), float(t),
+                     int(keep), int(parent))
 
 
 def fs_batch_submit(reqs, stream=None):
@@ -226,6 +237,64 @@ def fs_batch_submit(reqs, stream=None):
 def fs_batch_wait(ticket, timeout_us=-1):
     load()
     _check(_lib.fs_batch_wait(ctypes.c_uint64(ticket), int(timeout_us)), "fs_batch_wait")
+
+
+SERVE_STATS = ("batches", "completed", "max_in_flight", "overlapped_batches", "peak_bytes", "bytes_used",
+               "queued", "kept")
+
+
+def fs_serve_start(hbm_budget_bytes, slots=2, max_batch=64):
+    load()
+    _check(_lib.fs_serve_start(int(hbm_budget_bytes), int(slots), int(max_batch)), "fs_serve_start")
+
+
+def fs_serve_enqueue(req):
+    load()
+    t = ctypes.c_uint64()
+    _check(_lib.fs_serve_enqueue(ctypes.byref(req), ctypes.byref(t)), "fs_serve_enqueue")
+    return t.value
+
+
+def fs_serve_replay(reqs, arrival_s):
+    """Open-loop driver: enqueue reqs[i] at arrival_s[i] s; returns the tickets."""
+    load()
+    n = len(reqs)
+    arr = (FsRequest * n)(*reqs)
+    ts = (ctypes.c_double * n)(*[float(x) for x in arrival_s])
+    out = (ctypes.c_uint64 * n)()
+    _check(_lib.fs_serve_replay(arr, ts, n, out), "fs_serve_replay")
+    return [out[i] for i in range(n)]
+
+
+def fs_serve_poll(cap=1024, timeout_us=0):
+    """Finished tickets (possibly empty)."""
+    load()
+    buf = (ctypes.c_uint64 * cap)()
+    n = ctypes.c_int()
+    st = _lib.fs_serve_poll(buf, cap, ctypes.byref(n), int(timeout_us))
+    if st not in (FS_OK, -6):
+        _check(st, "fs_serve_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def fs_serve_latency(ticket):
+    load()
+    v = ctypes.c_double()
+    _check(_lib.fs_serve_latency(ctypes.c_uint64(ticket), ctypes.byref(v)), "fs_serve_latency")
+    return v.value
+
+
+def fs_serve_stats():
+    load()
+    n = len(SERVE_STATS)
+    buf = (ctypes.c_uint64 * n)()
+    _check(_lib.fs_serve_stats(buf, n), "fs_serve_stats")
+    return {SERVE_STATS[i]: int(buf[i]) for i in range(n)}
+
+
+def fs_serve_stop():
+    load()
+    _check(_lib.fs_serve_stop(), "fs_serve_stop")
 
 
 def fs_last_error():
