@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving leg")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -348,6 +350,13 @@ def run_ours(args, dist):
         "e2e": e2e, "roofline": roofline, "gpu_launches": int(launches), "clocks": clk,
         "comparators": comparators,
     }
+    if not args.no_serving:
+        # open-loop serving: 20,000 requests, N log-uniform in [128, 8192],
+        # mixed operators with follow-ups, 150 GB budget, arrival rate 0.8 x
+        # the plain per-call path's saturated throughput on the same mix
+        from paper_2412_12308_gb300 import servebench
+
+        line["serving"] = servebench.run(n_requests=args.serve_requests, load=0.8)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         gpu_out = out.cpu().numpy()
         line["cpu_baseline"] = cpu_baseline(u0, lx, ly, D, times, gpu_out)

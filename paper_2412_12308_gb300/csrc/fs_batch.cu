@@ -97,7 +97,8 @@ void drop_graph(Slot *s) {
 }  // namespace
 
 // ---------------------------------------------------------------- planning
-fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *const *keep_out) {
+fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *const *keep_out,
+                        long long direct_min_points) {
   bp->descs.clear();
   bp->units.clear();
   bp->arena_bytes = 0;
@@ -126,6 +127,17 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
     d.work_u = d.work_v = nullptr;
     d.fac = nullptr;
     d.out_u = r.out_u;
+    // column groups that fill a 512-thread batch CTA (the count does not
+    // change a column's arithmetic)
+    {
+      const int tseg = p->ny / p->rp_col.e;
+      int cc = kMaxThreads / tseg;
+      if (cc > 32) cc = 32;
+      if (cc < 1) cc = 1;
+      while (cc > 1 && (size_t)padded_len(cc * p->ny) * p->csize > 100 * 1024) cc >>= 1;
+      d.cols_per_unit = cc;
+      d.n_col_units = (p->M + 1 + cc - 1) / cc;
+    }
     switch (r.op) {
       case FS_OP_POISSON:
         if (!r.in_u) return set_error(FS_ERR_ARG, "fs_batch_submit: Poisson without input");
@@ -197,11 +209,14 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
   // stable largest-first order
   std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
   bp->descs.resize(n);
+  bp->direct.assign(n, 0);
   std::vector<int> slot_of(n);
   for (int k = 0; k < n; ++k) {
     slot_of[items[k].idx] = k;
     bp->descs[k] = ds[items[k].idx];
     bp->req_of_desc.push_back(items[k].idx);
+    const Desc &d = bp->descs[k];
+    if (direct_min_points > 0 && !d.small && (long long)d.nx * d.ny >= direct_min_points) bp->direct[k] = 1;
   }
   bp->ws_off.resize(n);
   for (int k = 0; k < n; ++k) bp->ws_off[k] = ws_off[items[k].idx];
@@ -221,6 +236,7 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
   auto emit_front = [&](int c) {
     for (int k = chunk_start[c]; k < chunk_start[c + 1]; ++k) {
       const Desc &d = bp->descs[k];
+      if (bp->direct[k]) continue;
       if (d.small) {
         bp->units.push_back(make_int4(k, K_SMALL, 0, 0));
         continue;
@@ -237,14 +253,14 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
   auto emit_col = [&](int c) {
     for (int k = chunk_start[c]; k < chunk_start[c + 1]; ++k) {
       const Desc &d = bp->descs[k];
-      if (d.small) continue;
+      if (d.small || bp->direct[k]) continue;
       for (int u = 0; u < d.n_col_units; ++u) bp->units.push_back(make_int4(k, K_COL, u, 0));
     }
   };
   auto emit_c2r = [&](int c) {
     for (int k = chunk_start[c]; k < chunk_start[c + 1]; ++k) {
       const Desc &d = bp->descs[k];
-      if (d.small) continue;
+      if (d.small || bp->direct[k]) continue;
       const int fields = (d.op == OP_WAVE_ADV && (d.flags & F_WANT_V)) ? 2 : 1;
       for (int f = 0; f < fields; ++f)
         for (int u = 0; u < d.n_row_units; ++u) bp->units.push_back(make_int4(k, K_C2R, u, f));
@@ -262,6 +278,29 @@ template <typename T>
 static size_t unit_smem(const Desc &d) {
   if (d.small) return Launch<T>::small_smem(d);
   return std::max(Launch<T>::row_smem(d), Launch<T>::col_smem(d));
+}
+
+// A problem run as standalone pass kernels (the per-call path) with the
+// batch's workspace pointers.
+template <typename T>
+static cudaError_t run_direct(const Desc &d0, cudaStream_t s) {
+  typedef Launch<T> L;
+  Desc d = d0;
+  // the standalone column kernels use the plan's column grouping
+  const int tseg = d.ny / d.rp_col.e;
+  int cc = 32;
+  while (cc > 1 && (cc * tseg > kMaxThreads || sizeof(cx<T>) * (size_t)padded_len(cc * d.ny) > 96 * 1024)) cc >>= 1;
+  if (sizeof(T) == 4 && d.rp_col.e == 16 && p2_col_ok(d.ny)) cc = p2_col_cnt(d.ny);
+  d.cols_per_unit = cc;
+  d.n_col_units = (d.M + 1 + cc - 1) / cc;
+  const bool diff = d.op == OP_DIFFUSION || d.op == OP_DIFF_ADV;
+  const bool adv = d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV;
+  cudaError_t e = cudaSuccess;
+  if (diff) e = L::factor(d, s);
+  if (e == cudaSuccess && !adv) e = L::rows(d, (d.op == OP_WAVE && (d.flags & F_HAS_V0)) ? 2 : 1, s);
+  if (e == cudaSuccess) e = L::cols(d, s);
+  if (e == cudaSuccess) e = L::c2r(d, (d.op == OP_WAVE_ADV && (d.flags & F_WANT_V)) ? 2 : 1, s);
+  return e;
 }
 
 // Resolve arena offsets into pointers and compute the launch's shared memory.
@@ -284,7 +323,7 @@ static size_t finish_descs(BatchPlan *bp, char *arena) {
                           (d.op == OP_WAVE_ADV && (d.flags & F_WANT_V));
       if (need_v) d.work_v = w;
     }
-    smem = std::max(smem, unit_smem<T>(d));
+    if (!bp->direct[k]) smem = std::max(smem, unit_smem<T>(d));
   }
   return smem;
 }
@@ -301,9 +340,9 @@ fs_status request_workspace(const fs_request &r, size_t *bytes) {
 }
 
 fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep_out, uint64_t *ticket_out,
-                                cudaStream_t stream, char *ext_arena, size_t ext_bytes) {
+                                cudaStream_t stream, char *ext_arena, size_t ext_bytes, long long direct_min_points) {
   BatchPlan bp;
-  fs_status st = plan_requests(reqs, n, &bp, keep_out);
+  fs_status st = plan_requests(reqs, n, &bp, keep_out, direct_min_points);
   if (st != FS_OK) return st;
   const unsigned long long wait_ns = (unsigned long long)env_ll("FS_BATCH_WAIT_NS", 2000000000LL);
   const bool inject = env_ll("FS_BATCH_INJECT_STALL", 0) != 0;
@@ -366,11 +405,28 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
   if (inject) {
     // test hook: make the first three-pass problem's column units wait for a
     // row tile that is never produced, so the bounded wait expires
-    for (Desc &d : bp.descs)
-      if (!d.small && d.op != OP_DIFF_ADV && d.op != OP_WAVE_ADV) {
+    for (size_t k = 0; k < nd; ++k) {
+      Desc &d = bp.descs[k];
+      if (!d.small && !bp.direct[k] && d.op != OP_DIFF_ADV && d.op != OP_WAVE_ADV) {
         d.n_row_units += 1;
         break;
       }
+    }
+  }
+  // problems above the direct threshold: standalone pass kernels, in order
+  for (size_t k = 0; k < nd; ++k) {
+    if (!bp.direct[k]) continue;
+    e = dtype == FS_F64 ? run_direct<double>(bp.descs[k], stream) : run_direct<float>(bp.descs[k], stream);
+    if (e != cudaSuccess) return cuda_error(e, "batch: standalone pass launch");
+  }
+  if (nu == 0) {
+    s->h_status[0] = s->h_status[1] = 0;
+    e = cudaEventRecord(s->ev, stream);
+    if (e != cudaSuccess) return cuda_error(e, "batch: event record");
+    s->pending = true;
+    s->ticket = g_next_ticket++;
+    if (ticket_out) *ticket_out = s->ticket;
+    return FS_OK;
   }
   memcpy(s->h_descs, bp.descs.data(), nd * sizeof(Desc));
   memcpy(s->h_units, bp.units.data(), nu * sizeof(int4));

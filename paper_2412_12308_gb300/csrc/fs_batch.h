@@ -13,6 +13,7 @@ struct BatchPlan {
   std::vector<int> req_of_desc;  // request index of each desc
   std::vector<size_t> ws_off;    // arena offset of each desc's workspace
   std::vector<int4> units;       // work table: (desc, kind, index, field)
+  std::vector<char> direct;      // desc runs as standalone pass kernels, not units
   size_t arena_bytes = 0;
   size_t smem = 0;
   int dtype = -1;
@@ -21,13 +22,17 @@ struct BatchPlan {
 // Validate requests and build descriptors + work table (no device work).
 // keep_out[i] (optional): device buffer that receives request i's forward
 // half spectrum (diffusion / wave solves with zero initial velocity).
-fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *const *keep_out = nullptr);
+// direct_min_points > 0: problems with nx*ny >= it run as standalone pass
+// kernels (before the persistent launch) instead of work units.
+fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *const *keep_out = nullptr,
+                        long long direct_min_points = 0);
 
 // Submit a planned batch on `stream` (see fs_batch_submit).
 // ext_arena (optional, >= the batch's workspace bytes) replaces the slot's own
 // arena; *ws_bytes_out (optional) receives the batch's workspace bytes.
 fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep_out, uint64_t *ticket_out,
-                                cudaStream_t stream, char *ext_arena = nullptr, size_t ext_bytes = 0);
+                                cudaStream_t stream, char *ext_arena = nullptr, size_t ext_bytes = 0,
+                                long long direct_min_points = 0);
 
 // Workspace bytes one request needs in a batch arena (validates it).
 fs_status request_workspace(const fs_request &r, size_t *bytes);

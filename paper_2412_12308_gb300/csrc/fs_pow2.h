@@ -18,6 +18,17 @@ constexpr int p2_row_cnt(int M) {
 }
 constexpr bool p2_row_ok(int M) { return M >= 128 && M <= 4096 && (M & (M - 1)) == 0; }
 
+// Device-side unit functions for the persistent batch and single-CTA paths
+// (row tiles must use p2_row_cnt(M) rows; columns take any count).  Return
+// false when the length is not specialised.
+template <typename T>
+struct cx;
+__device__ bool p2_unit_r2c(const Desc &d, int unit, int cnt, cx<float> *sm, const float *in, cx<float> *spec);
+__device__ bool p2_unit_c2r(const Desc &d, int unit, int cnt, cx<float> *sm, const cx<float> *spec, float *out,
+                            bool sh);
+__device__ bool p2_unit_col1(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu, cx<float> *wv,
+                             bool sh);
+
 // Kernel lookup (nullptr when not specialised).
 PassKernel p2_r2c_f32(int M);
 PassKernel p2_c2r_f32(int M);

@@ -164,6 +164,64 @@ __global__ void __launch_bounds__(ColT<L>::THREADS, min_blocks<ColT<L>::THREADS>
 #define FS_P2_ROWS(X) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 #define FS_P2_COLS(X) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
 
+// ---------------------------------------------------------------- device dispatch for batch / small paths
+template <int M>
+__device__ __noinline__ void p2_r2c_unit(const Desc &d, int unit, cx<float> *sm, const float *in, cx<float> *spec) {
+  unit_row_r2c_t<float, 16, M, RowK<M>::CC>(d, unit, RowK<M>::CC, sm, in, spec);
+}
+template <int M>
+__device__ __noinline__ void p2_c2r_unit(const Desc &d, int unit, cx<float> *sm, const cx<float> *spec, float *out,
+                                         bool sh) {
+  unit_row_c2r_t<float, 16, M, RowK<M>::CC>(d, unit, RowK<M>::CC, sm, spec, out, sh);
+}
+template <int L>
+__device__ __noinline__ void p2_col1_unit(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu,
+                                          cx<float> *wv, bool sh) {
+  unit_col_t<float, 16, false, L, 0>(d, unit, cnt, sm, wu, wv, sh);
+}
+
+__device__ bool p2_unit_r2c(const Desc &d, int unit, int cnt, cx<float> *sm, const float *in, cx<float> *spec) {
+  if (d.rp_row.e != 16 || cnt != p2_row_cnt(d.M)) return false;
+  switch (d.M) {
+#define C(m)                                 \
+  case m:                                    \
+    p2_r2c_unit<m>(d, unit, sm, in, spec);   \
+    return true;
+    FS_P2_ROWS(C)
+#undef C
+    default:
+      return false;
+  }
+}
+__device__ bool p2_unit_c2r(const Desc &d, int unit, int cnt, cx<float> *sm, const cx<float> *spec, float *out,
+                            bool sh) {
+  if (d.rp_row.e != 16 || cnt != p2_row_cnt(d.M)) return false;
+  switch (d.M) {
+#define C(m)                                        \
+  case m:                                           \
+    p2_c2r_unit<m>(d, unit, sm, spec, out, sh);     \
+    return true;
+    FS_P2_ROWS(C)
+#undef C
+    default:
+      return false;
+  }
+}
+__device__ bool p2_unit_col1(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu, cx<float> *wv,
+                             bool sh) {
+  if (d.rp_col.e != 16) return false;
+  switch (d.ny) {
+#define C(l)                                           \
+  case l:                                              \
+    p2_col1_unit<l>(d, unit, cnt, sm, wu, wv, sh);     \
+    return true;
+    FS_P2_COLS(C)
+#undef C
+    default:
+      return false;
+  }
+}
+
 PassKernel p2_r2c_f32(int M) {
   switch (M) {
 #define C(m) \

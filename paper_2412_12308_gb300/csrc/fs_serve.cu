@@ -14,6 +14,7 @@
 // completion, per request.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -122,6 +123,7 @@ struct Server {
   std::thread th;
   uint64_t next_ticket = 1;
   size_t queue_cap = 1u << 20;
+  long long direct_min_points = 2048LL * 2048LL;  // grids this large run as standalone passes
   // statistics
   uint64_t n_batches = 0, n_done = 0, max_inflight = 0, overlap_batches = 0;
   fs_status last_error = FS_OK;
@@ -270,7 +272,7 @@ bool launch_one_locked(Server *S) {
   S->peak_used = std::max(S->peak_used, S->used);
   uint64_t bt = 0;
   fs_status st = batch_submit_internal(reqs.data(), (int)reqs.size(), keeps.data(), &bt, S->streams[slot],
-                                       ws ? S->arena.base + f.ws_off : nullptr, ws);
+                                       ws ? S->arena.base + f.ws_off : nullptr, ws, S->direct_min_points);
   cudaError_t e = cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(f.ev, S->streams[slot]);
   if (st != FS_OK || e != cudaSuccess) S->last_error = st != FS_OK ? st : FS_ERR_CUDA;
@@ -314,6 +316,7 @@ extern "C" fs_status fs_serve_start(size_t hbm_budget_bytes, int slots, int max_
   Server *S = new Server();
   S->budget = al256(hbm_budget_bytes);
   S->max_batch = max_batch;
+  if (const char *v = getenv("FS_SERVE_DIRECT_MIN")) S->direct_min_points = atoll(v);
   cudaError_t e = cudaGetDevice(&S->device);
   if (e == cudaSuccess) e = S->arena.init(S->budget);
   for (int i = 0; e == cudaSuccess && i < slots; ++i) {

@@ -482,6 +482,29 @@ inline PassKernels pass_kernels<double>(int e) {
   switch (e) { FS_FOR_EACH_E_double(FS_PK_CASE) default: return PassKernels{}; }
 }
 
+// Compile-time power-of-two units (FP32 only; defined in fs_pow2_f32.cu).
+__device__ __forceinline__ bool pow2_r2c(const Desc &d, int unit, int cnt, cx<float> *sm, const float *in,
+                                         cx<float> *spec) {
+  return p2_unit_r2c(d, unit, cnt, sm, in, spec);
+}
+__device__ __forceinline__ bool pow2_r2c(const Desc &, int, int, cx<double> *, const double *, cx<double> *) {
+  return false;
+}
+__device__ __forceinline__ bool pow2_c2r(const Desc &d, int unit, int cnt, cx<float> *sm, const cx<float> *spec,
+                                         float *out, bool sh) {
+  return p2_unit_c2r(d, unit, cnt, sm, spec, out, sh);
+}
+__device__ __forceinline__ bool pow2_c2r(const Desc &, int, int, cx<double> *, const cx<double> *, double *, bool) {
+  return false;
+}
+__device__ __forceinline__ bool pow2_col1(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu,
+                                          cx<float> *wv, bool sh) {
+  return p2_unit_col1(d, unit, cnt, sm, wu, wv, sh);
+}
+__device__ __forceinline__ bool pow2_col1(const Desc &, int, int, cx<double> *, cx<double> *, cx<double> *, bool) {
+  return false;
+}
+
 template <typename T>
 struct Units;
 #define FS_UNITS_SPEC(T)                                                                        \
@@ -489,10 +512,12 @@ struct Units;
   struct Units<T> {                                                                             \
     static __device__ __forceinline__ void r2c(const Desc &d, int unit, int cnt, cx<T> *sm,     \
                                                const T *in, cx<T> *spec) {                      \
+      if (pow2_r2c(d, unit, cnt, sm, in, spec)) return;                                         \
       FS_E_SWITCH_##T(d.rp_row.e, unit_row_r2c, d, unit, cnt, sm, in, spec)                      \
     }                                                                                           \
     static __device__ __forceinline__ void c2r(const Desc &d, int unit, int cnt, cx<T> *sm,     \
                                                const cx<T> *spec, T *out, bool sh) {            \
+      if (pow2_c2r(d, unit, cnt, sm, spec, out, sh)) return;                                    \
       FS_E_SWITCH_##T(d.rp_row.e, unit_row_c2r, d, unit, cnt, sm, spec, out, sh)                 \
     }                                                                                           \
     static __device__ __forceinline__ void col(const Desc &d, int unit, int cnt, cx<T> *sm,     \
@@ -500,6 +525,7 @@ struct Units;
       if (col_two_fields(d)) {                                                                  \
         FS_E_SWITCH_##T(d.rp_col.e, unit_col2, d, unit, cnt, sm, wu, wv, sh)                    \
       } else {                                                                                  \
+        if (pow2_col1(d, unit, cnt, sm, wu, wv, sh)) return;                                    \
         FS_E_SWITCH_##T(d.rp_col.e, unit_col, d, unit, cnt, sm, wu, wv, sh)                     \
       }                                                                                         \
     }                                                                                           \

@@ -1,0 +1,170 @@
+"""Open-loop serving measurement (CUDA path only).
+
+Stream (workloads.serve_stream): N log-uniform in [128, 8192] snapped to a
+supported size, operators uniform over {Poisson, diffusion, wave}; every
+diffusion / wave request keeps its spectrum and is followed, after an
+exponential delay (mean 10 ms), by one advance to a later time on that
+spectrum.  Exponential inter-arrival gaps; the rate is `load` times the
+saturated throughput of the plain path on the same mix.
+
+Plain path: one request at a time through the per-call entry points on one
+stream (solve; or kept-state reset + advance; follow-up = advance).  Its
+per-(size, kind) service time is measured with CUDA events; its saturated
+rate is requests / sum of service times, and its latency under the same
+arrivals is the FIFO single-server recursion finish_i = max(arrival_i,
+finish_{i-1}) + service_i.
+
+Served path: fs_serve_replay enqueues each request at its arrival time; the
+server batches whatever is queued whenever one of its in-flight slots frees.
+Latency = enqueue -> observed completion (fs_serve_latency).
+"""
+
+import time
+
+import numpy as np
+
+
+def _percentiles(x):
+    x = np.asarray(x, dtype=np.float64)
+    return {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
+            "mean_us": float(x.mean())}
+
+
+def run(n_requests=20000, load=0.8, seed=12312, budget_bytes=150 << 30, slots=3, max_batch=32,
+        nmin=128, nmax=8192, pool=3, verbose=False):
+    import torch
+
+    from . import fsolve as fs
+    from . import workloads as wl
+
+    fs.load()
+    base = wl.serve_stream(1.0, seed=seed, count=n_requests, nmin=nmin, nmax=nmax)
+    sizes = sorted({r.problem.n for r in base})
+    plans, inputs, outs, states = {}, {}, {}, {}
+    rng = np.random.default_rng(seed)
+    for n in sizes:
+        plans[n] = fs.fs_plan_create(n, n, 1.0, 1.0, fs.FS_F32)
+        f = wl.mode_sum(wl.draw_modes(rng, 8, min(16, n // 2 - 1)), n, n, 1.0, 1.0).astype(np.float32)
+        inputs[n] = torch.tensor(f, device="cuda")
+        outs[n] = [torch.empty_like(inputs[n]) for _ in range(pool)]
+        states[n] = fs.fs_state_create(plans[n], inputs[n])
+    ops = {"poisson": fs.FS_OP_POISSON, "diffusion": fs.FS_OP_DIFFUSION, "wave": fs.FS_OP_WAVE}
+
+    # ---- plain path service times per (size, kind)
+    def plain_call(n, kind, out):
+        if kind == "poisson":
+            fs.fs_poisson_solve(plans[n], inputs[n], out)
+        elif kind in ("diffusion", "wave"):  # first request: forward into the kept state + advance
+            fs.fs_state_reset(states[n], inputs[n])
+            if kind == "diffusion":
+                fs.fs_diffusion_advance(states[n], 0.1, 0.3, out)
+            else:
+                fs.fs_wave_advance(states[n], 1.0, 0.3, out)
+        elif kind == "diffusion_adv":
+            fs.fs_diffusion_advance(states[n], 0.1, 0.6, out)
+        else:
+            fs.fs_wave_advance(states[n], 1.0, 0.6, out)
+
+    service = {}
+    for n in sizes:
+        for kind in ("poisson", "diffusion", "wave", "diffusion_adv", "wave_adv"):
+            for _ in range(2):
+                plain_call(n, kind, outs[n][0])
+            torch.cuda.synchronize()
+            reps = 5 if n >= 4096 else 10
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                plain_call(n, kind, outs[n][0])
+            b.record()
+            torch.cuda.synchronize()
+            service[(n, kind)] = a.elapsed_time(b) / reps / 1e3  # seconds
+    # ---- the request list (initial requests + follow-ups), sorted by arrival
+    items = []  # (arrival, kind, n, D, c, t, parent_key, key)
+    for r in base:
+        p = r.problem
+        items.append([r.arrival_s, p.op, p.n, p.D, p.c, p.t, None, ("a", r.rid)])
+        if r.followup_t >= 0:
+            items.append([r.arrival_s + r.followup_delay_s, p.op + "_adv", p.n, p.D, p.c, r.followup_t,
+                          ("a", r.rid), ("f", r.rid)])
+    n_total = len(items)
+    plain_total = sum(service[(it[2], it[1])] for it in items)
+    plain_rate = n_total / plain_total
+    # scale the arrival clock so the offered load is `load` x the plain path's capacity
+    span = max(r.arrival_s for r in base)
+    target_span = n_total / (load * plain_rate)
+    scale = target_span / span
+    for it in items:
+        it[0] *= scale
+    items.sort(key=lambda it: it[0])
+    # plain path latency under the same arrivals (FIFO single server)
+    fin = 0.0
+    plain_lat = []
+    for it in items:
+        start = max(it[0], fin)
+        fin = start + service[(it[2], it[1])]
+        plain_lat.append((fin - it[0]) * 1e6)
+    plain_makespan = fin - items[0][0]
+    # ---- served path
+    index = {it[7]: i for i, it in enumerate(items)}
+    reqs = []
+    counters = {n: 0 for n in sizes}
+    for i, it in enumerate(items):
+        arrival, kind, n, D, c, t, parent, key = it
+        out = outs[n][counters[n] % pool]
+        counters[n] += 1
+        if kind.endswith("_adv"):
+            op = fs.FS_OP_DIFFUSION_ADVANCE if kind.startswith("diffusion") else fs.FS_OP_WAVE_ADVANCE
+            reqs.append(fs.fs_request(op, out_u=out, D=D, c=c, t=t, parent=index[parent] + 1))
+        else:
+            keep = 0 if kind == "poisson" else 1
+            reqs.append(fs.fs_request(ops[kind], plan=plans[n], in_u=inputs[n], out_u=out, D=D, c=c, t=t,
+                                      keep=keep))
+    arrivals = [it[0] for it in items]
+    fs.fs_serve_start(budget_bytes, slots=slots, max_batch=max_batch)
+    try:
+        t0 = time.perf_counter()
+        tickets = fs.fs_serve_replay(reqs, arrivals)
+        pending = set(tickets)
+        while pending:
+            for t in fs.fs_serve_poll(8192, 200_000):
+                pending.discard(t)
+            if time.perf_counter() - t0 > 600:
+                raise RuntimeError(f"serving: {len(pending)} requests unfinished after 600 s")
+        makespan = time.perf_counter() - t0
+        lat = [fs.fs_serve_latency(t) for t in tickets]
+        stats = fs.fs_serve_stats()
+    finally:
+        fs.fs_serve_stop()
+        for n in sizes:
+            fs.fs_state_destroy(states[n])
+            fs.fs_plan_destroy(plans[n])
+    res = {
+        "requests": n_total, "initial_requests": len(base), "load": load,
+        "rate_per_s": n_total / (arrivals[-1] - arrivals[0]),
+        "served": {"solves_per_s": n_total / makespan, **_percentiles(lat), "batches": stats["batches"],
+                   "max_in_flight": stats["max_in_flight"], "peak_hbm_bytes": stats["peak_bytes"]},
+        "plain_path": {"saturated_solves_per_s": plain_rate, "solves_per_s": n_total / plain_makespan,
+                       **_percentiles(plain_lat), "what": "one request at a time via the per-call entry points, "
+                                                          "FIFO queue with measured service times"},
+        "budget_bytes": budget_bytes, "slots": slots, "max_batch": max_batch,
+        "sizes": [int(n) for n in sizes],
+    }
+    if verbose:
+        print(res)
+    return res
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=20000)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--slots", type=int, default=3)
+    ap.add_argument("--max-batch", type=int, default=32)
+    a = ap.parse_args()
+    print(json.dumps(run(a.requests, a.load, budget_bytes=int(a.budget_gb * (1 << 30)), slots=a.slots,
+                         max_batch=a.max_batch)))
