@@ -165,7 +165,9 @@ typedef struct fs_request {
  * from a device work table through an atomic counter; a unit waits (bounded:
  * 2 s per wait by default, env FS_BATCH_WAIT_NS; expiry sets FS_ERR_TIMEOUT in
  * the batch status and the kernel exits) only for units of its own problem
- * listed before it.  Workspace comes from a library-owned arena per in-flight
+ * listed before it.  Problems of 4096^2 points or more (env FS_BATCH_DIRECT_MIN)
+ * fill the GPU on their own and run as the standalone pass kernels, in order,
+ * before that launch.  Workspace comes from a library-owned arena per in-flight
  * batch.  Each problem's result depends only on its own request (same tile
  * shapes and unit code alone or in any mix), so it is bit-identical across
  * batches.  The call enqueues on `stream` and returns; *ticket_out names the

@@ -3,6 +3,8 @@
     python -m paper_2412_12308_gb300.cases poisson --n 4096 --iters 20
     python -m paper_2412_12308_gb300.cases wave_adv --n 4096 --iters 20
     python -m paper_2412_12308_gb300.cases diffusion_batch --n 1024 --iters 5
+    python -m paper_2412_12308_gb300.cases batch_mix --iters 5
+    python -m paper_2412_12308_gb300.cases wave_snapshots --n 4096 --iters 5
 
 Each case runs `--warmup` untimed repetitions, then `--iters` timed ones
 (CUDA events on the current stream) and prints one JSON line with the mean
@@ -64,6 +66,40 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
         def rep():
             fsolve.fs_diffusion_advance(state, 0.1, 0.37, out)
         algo = 2 * spec + spec + real
+    elif case == "batch_mix":
+        # 512 uneven problems (N in {64..2048}, all three operators) in one
+        # persistent launch per repetition
+        probs = workloads_batch_mix()
+        bplans, ins, outs_b = {}, [], []
+        for pr in probs:
+            if pr.n not in bplans:
+                bplans[pr.n] = fs.fs_plan_create(pr.n, pr.n, pr.lx, pr.ly, fs.FS_F32)
+            ins.append(torch.tensor(pr.field(np.float32), device="cuda"))
+            outs_b.append(torch.empty_like(ins[-1]))
+        ops = {"poisson": fs.FS_OP_POISSON, "diffusion": fs.FS_OP_DIFFUSION, "wave": fs.FS_OP_WAVE}
+        reqs = [fs.fs_request(ops[pr.op], plan=bplans[pr.n], in_u=ins[i], out_u=outs_b[i], D=pr.D, c=pr.c, t=pr.t)
+                for i, pr in enumerate(probs)]
+
+        def rep():
+            fsolve.fs_batch_submit(reqs)
+        pts = sum(pr.n * pr.n for pr in probs)
+        algo = sum(3 * (pr.n * pr.n * 4 + (pr.n // 2 + 1) * pr.n * 8) for pr in probs)
+        extra["solves_per_rep"] = len(probs)
+        extra["mean_points"] = pts / len(probs)
+        extra["_cleanup"] = bplans
+    elif case == "wave_snapshots":
+        # 1 forward transform into the kept spectrum + 50 snapshots t = j/50
+        nt = 50
+        state = fsolve.fs_state_create(plan, fd)
+        outs = torch.empty((nt, n, n), dtype=fd.dtype, device="cuda")
+        reqs = [fs.fs_request(fs.FS_OP_WAVE_ADVANCE, state=state, out_u=outs[j], c=1.0, t=(j + 1) / nt)
+                for j in range(nt)]
+
+        def rep():
+            fsolve.fs_state_reset(state, fd)
+            fsolve.fs_batch_submit(reqs)
+        algo = (real + 2 * spec) + nt * (3 * spec + real)
+        extra["solves_per_rep"] = nt
     elif case == "diffusion_batch":
         nt = 100
         state = fsolve.fs_state_create(plan, fd)
@@ -90,7 +126,10 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
     ms = a.elapsed_time(b) / iters
     res = {"case": case, "n": n, "dtype": dtype, "iters": iters, "ms_per_rep": round(ms, 5),
            "algorithmic_bytes": algo, "algorithmic_GBps": round(algo / (ms / 1e3) / 1e9, 1)}
+    cleanup = extra.pop("_cleanup", None)
     res.update(extra)
+    if "solves_per_rep" in extra:
+        res["solves_per_s"] = round(extra["solves_per_rep"] / (ms / 1e3), 1)
     if profile:
         fsolve.fs_profile_enable(True)
         for _ in range(iters):
@@ -101,8 +140,16 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
         res["per_kernel_us"] = {k: round(1e3 * v[1] / v[0], 3) for k, v in prof.items() if v[0]}
     if state is not None:
         fsolve.fs_state_destroy(state)
+    for h in (cleanup or {}).values():
+        fsolve.fs_plan_destroy(h)
     fsolve.fs_plan_destroy(plan)
     return res
+
+
+def workloads_batch_mix():
+    from . import workloads
+
+    return workloads.batch_mix()
 
 
 def main():

@@ -493,7 +493,11 @@ using namespace fs;
 extern "C" fs_status fs_batch_submit(const fs_request *reqs, int n, uint64_t *ticket_out, fs_stream stream) {
   if (ticket_out) *ticket_out = 0;
   if (!reqs || n <= 0) return set_error(FS_ERR_ARG, "fs_batch_submit: empty batch");
-  return batch_submit_internal(reqs, n, nullptr, ticket_out, reinterpret_cast<cudaStream_t>(stream));
+  // grids of 4096^2 points and more already fill the GPU on their own: they
+  // run as the standalone pass kernels, in order, before the persistent launch
+  const long long direct_min = env_ll("FS_BATCH_DIRECT_MIN", 4096LL * 4096LL);
+  return batch_submit_internal(reqs, n, nullptr, ticket_out, reinterpret_cast<cudaStream_t>(stream), nullptr, 0,
+                               direct_min);
 }
 
 extern "C" fs_status fs_batch_wait(uint64_t ticket, int timeout_us) {
