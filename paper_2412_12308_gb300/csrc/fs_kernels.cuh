@@ -228,6 +228,13 @@ struct Launch {
     return launch(k, d.n_row_units * fields, row_threads(d), row_smem(d), d, s, PC_R2C);
   }
   static cudaError_t cols(const Desc &d, cudaStream_t s) {
+    // measured variant: split-BF16 tensor-core first stage (advances only)
+    if (sizeof(T) == 4 && tc_variant_requested() && !col_two_fields(d) && d.rp_col.e == 16 &&
+        (d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV)) {
+      size_t sm = 0;
+      PassKernel k = p2_col_tc_f32(d.ny, &sm);
+      if (k) return launch(k, d.M + 1, d.ny / 16, sm, d, s, PC_COL);
+    }
     // TMA-staged persistent kernel for single-field FP32 power-of-two columns
     if (sizeof(T) == 4 && !col_two_fields(d) && p2_col(d) && tma_enabled()) {
       PassKernel k = p2_col_tma_f32(d.ny);

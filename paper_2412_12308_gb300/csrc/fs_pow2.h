@@ -36,6 +36,9 @@ PassKernel p2_col1_f32(int L);
 PassKernel p2_col2_f32(int L);
 // TMA-staged persistent column kernel (single field) and its shared memory.
 PassKernel p2_col_tma_f32(int L);
+// Split-BF16 tensor-core first stage (measured variant, FS_COLUMN_VARIANT=bf16x3).
+bool tc_variant_requested();
+PassKernel p2_col_tc_f32(int L, size_t *smem);
 size_t p2_col_tma_smem(int L);
 
 }  // namespace fs
