@@ -177,6 +177,7 @@ Desc base_desc(const fs_plan_s *p) {
   d.n_row_units = (p->ny + d.rows_per_unit - 1) / d.rows_per_unit;
   d.n_col_units = (p->M + 1 + d.cols_per_unit - 1) / d.cols_per_unit;
   d.n_fac_units = (p->M + 1 + p->ny + kFactorPerUnit - 1) / kFactorPerUnit;
+  d.row_g = d.col_g = 1;
   d.small_rows = p->tc.small_rows;
   d.small_cols = p->tc.small_cols;
   d.rp_row = p->rp_row;

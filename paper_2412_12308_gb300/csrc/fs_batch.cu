@@ -221,6 +221,31 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
   bp->ws_off.resize(n);
   for (int k = 0; k < n; ++k) bp->ws_off[k] = ws_off[items[k].idx];
 
+  // Work-unit granularity: each unit covers G row tiles / column groups, G
+  // chosen so the batch still has several units per SM (grouping does not
+  // change any problem's arithmetic).
+  {
+    long long tiles = 0;
+    for (int k = 0; k < n; ++k) {
+      const Desc &d = bp->descs[k];
+      if (d.small || bp->direct[k]) continue;
+      tiles += (d.ny + d.rows_per_unit - 1) / d.rows_per_unit;
+      tiles += (d.M + 1 + d.cols_per_unit - 1) / d.cols_per_unit;
+    }
+    // measured on GB300: 2-4 groups per unit beat 1 (per-unit overhead) and 8
+    // (too few units to balance); aim for ~24 units per SM
+    int G = (int)(tiles / (24LL * 152LL));
+    G = G < 1 ? 1 : (G > 4 ? 4 : G);
+    if (const char *v = getenv("FS_BATCH_GROUP")) G = atoi(v) > 0 ? atoi(v) : G;
+    for (int k = 0; k < n; ++k) {
+      Desc &d = bp->descs[k];
+      d.row_g = d.col_g = G;
+      const int rt = (d.ny + d.rows_per_unit - 1) / d.rows_per_unit;
+      const int cg = (d.M + 1 + d.cols_per_unit - 1) / d.cols_per_unit;
+      d.n_row_units = (rt + G - 1) / G;
+      d.n_col_units = (cg + G - 1) / G;
+    }
+  }
   // chunks by intermediate bytes
   std::vector<int> chunk_start;
   size_t acc = 0;
@@ -286,6 +311,8 @@ template <typename T>
 static cudaError_t run_direct(const Desc &d0, cudaStream_t s) {
   typedef Launch<T> L;
   Desc d = d0;
+  d.row_g = d.col_g = 1;
+  d.n_row_units = (d.ny + d.rows_per_unit - 1) / d.rows_per_unit;
   // the standalone column kernels use the plan's column grouping
   const int tseg = d.ny / d.rp_col.e;
   int cc = 32;

@@ -43,6 +43,7 @@ struct Desc {
   int32_t n_row_units;        // per field
   int32_t n_col_units;
   int32_t n_fac_units;
+  int32_t row_g, col_g;       // batch: row tiles / column groups per work unit (>= 1)
   int32_t small;              // 1: whole problem in one CTA (shared-memory resident)
   int32_t small_rows;         // row group of the small path
   int32_t small_cols;         // column group of the small path

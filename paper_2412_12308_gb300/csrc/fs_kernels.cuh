@@ -78,10 +78,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch(const Desc *__restrict__ 
   __shared__ Desc sd;
   __shared__ int s_unit, s_abort;
   cx<T> *sm = reinterpret_cast<cx<T> *>(fs_smem);
+  __shared__ int s_next;
+  if (threadIdx.x == 0) s_next = atomicAdd(&ctl[0], 1);
   for (;;) {
     if (threadIdx.x == 0) {
-      s_unit = atomicAdd(&ctl[0], 1);
+      s_unit = s_next;
       s_abort = 0;
+      // the next unit index is fetched while this one runs (indices are taken
+      // and run in increasing order per CTA, so dependencies stay backward)
+      if (s_unit < n_units) s_next = atomicAdd(&ctl[0], 1);
     }
     __syncthreads();
     const int k = s_unit;
@@ -141,23 +146,39 @@ __global__ void __launch_bounds__(kMaxThreads) k_batch(const Desc *__restrict__ 
       case K_FACTOR:
         unit_factor<T>(d, u.z * kFactorPerUnit, kFactorPerUnit, blockDim.x);
         break;
-      case K_ROW:
-        row_r2c_any<T>(d, u.z, d.rows_per_unit, sm,
-                              reinterpret_cast<const T *>(u.w ? d.in_v : d.in_u),
-                              reinterpret_cast<cx<T> *>(u.w ? d.work_v : d.work_u));
+      case K_ROW: {
+        const int tiles = (d.ny + d.rows_per_unit - 1) / d.rows_per_unit;
+        for (int g = 0; g < d.row_g; ++g) {
+          const int tile = u.z * d.row_g + g;
+          if (tile >= tiles) break;
+          row_r2c_any<T>(d, tile, d.rows_per_unit, sm, reinterpret_cast<const T *>(u.w ? d.in_v : d.in_u),
+                         reinterpret_cast<cx<T> *>(u.w ? d.work_v : d.work_u));
+        }
         break;
+      }
       case K_SMALL:
         unit_small<T>(d, sm);
         break;
-      case K_COL:
-        col_any<T>(d, u.z, d.cols_per_unit, sm, reinterpret_cast<cx<T> *>(d.work_u),
-                   reinterpret_cast<cx<T> *>(d.work_v), false);
+      case K_COL: {
+        const int groups = (d.M + 1 + d.cols_per_unit - 1) / d.cols_per_unit;
+        for (int g = 0; g < d.col_g; ++g) {
+          const int grp = u.z * d.col_g + g;
+          if (grp >= groups) break;
+          col_any<T>(d, grp, d.cols_per_unit, sm, reinterpret_cast<cx<T> *>(d.work_u),
+                     reinterpret_cast<cx<T> *>(d.work_v), false);
+        }
         break;
-      case K_C2R:
-        row_c2r_any<T>(d, u.z, d.rows_per_unit, sm,
-                       reinterpret_cast<const cx<T> *>(u.w ? d.work_v : d.work_u),
-                       reinterpret_cast<T *>(u.w ? d.out_v : d.out_u), false);
+      }
+      case K_C2R: {
+        const int tiles = (d.ny + d.rows_per_unit - 1) / d.rows_per_unit;
+        for (int g = 0; g < d.row_g; ++g) {
+          const int tile = u.z * d.row_g + g;
+          if (tile >= tiles) break;
+          row_c2r_any<T>(d, tile, d.rows_per_unit, sm, reinterpret_cast<const cx<T> *>(u.w ? d.work_v : d.work_u),
+                         reinterpret_cast<T *>(u.w ? d.out_v : d.out_u), false);
+        }
         break;
+      }
       default:
         break;
     }
