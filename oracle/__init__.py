@@ -28,6 +28,10 @@ Pinning status (what fixes each function independently of itself):
                            time reversal, period return             -> pinned
   closed_forms.*           cross-checked against each other via the solves
                            above and by finite differences of the PDE -> pinned
+  solve.*_source_spectrum  constant-source forms: the PDE residual by time
+                           finite differences and a spectral Laplacian from
+                           numpy.fft, initial conditions, zero-mode
+                           polynomials                               -> pinned
 """
 
 from .dft import dft1, dft2, idft2, dft_matrix  # noqa: F401
@@ -41,5 +45,7 @@ from .solve import (  # noqa: F401
     wave,
     wave_spectrum,
     state_spectrum,
+    diffusion_source_spectrum,
+    wave_source_spectrum,
 )
 from . import closed_forms  # noqa: F401

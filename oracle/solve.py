@@ -34,6 +34,8 @@ import numpy as np
 from .dft import dft2, idft2
 
 __all__ = [
+    "diffusion_source_spectrum",
+    "wave_source_spectrum",
     "omega_axis",
     "omega2",
     "state_spectrum",
@@ -154,3 +156,41 @@ def wave(u0, v0, c, t, lx, ly, sign=-1, want_v=False):
         return u
     v = _real_part(idft2(V, sign=-sign), "wave v")
     return u, v
+
+
+# ---------------------------------------------------------------- constant sources
+# Eq. DiffusionIVPFS and Eq. WaveEquationFourierSpace with a time-independent
+# source s.  Each mode is a linear ODE with constant forcing:
+#   diffusion  dU/dt = -D w^2 U + S      ->  U = F E + S (1 - E) / (D w^2),
+#              E = exp(-D w^2 t);  w = 0: U = F + S t
+#   wave       U'' + c^2 w^2 U = S       ->  U = S/(c w)^2 + (F - S/(c w)^2) cos(c w t)
+#                                                + G sin(c w t) / (c w);
+#              w = 0: U = F + G t + S t^2 / 2  (Eq. OmegaZero)
+# The printed Eq. OmegaNonZero omits the particular term S/w^2 added outside the
+# cosine; the form above satisfies the ODE and the initial conditions.
+def diffusion_source_spectrum(F, S, D, t, lx, ly):
+    ny, nx = F.shape
+    w2 = omega2(nx, ny, lx, ly)
+    lam = float(D) * w2
+    E = np.exp(-lam * float(t))
+    gain = np.empty_like(w2)
+    nz = lam > 0.0
+    gain[nz] = -np.expm1(-lam[nz] * float(t)) / lam[nz]
+    gain[~nz] = float(t)
+    return F * E + S * gain
+
+
+def wave_source_spectrum(F, G, S, c, t, lx, ly):
+    """(U(t), V(t)) with initial velocity spectrum G (or None) and source S."""
+    U, V = wave_spectrum(F, G, c, t, lx, ly)
+    ny, nx = F.shape
+    cw = float(c) * np.sqrt(omega2(nx, ny, lx, ly))
+    th = cw * float(t)
+    pu = np.empty_like(cw)
+    pv = np.empty_like(cw)
+    nz = cw > 0.0
+    pu[nz] = 2.0 * np.sin(0.5 * th[nz]) ** 2 / cw[nz] ** 2  # (1 - cos th) / (c w)^2
+    pv[nz] = np.sin(th[nz]) / cw[nz]
+    pu[~nz] = 0.5 * float(t) ** 2
+    pv[~nz] = float(t)
+    return U + S * pu, V + S * pv

@@ -267,6 +267,59 @@ def pin_sign_independence(n=24, seed=12):
     return max(worst, rel(a, b))
 
 
+# ----------------------------------------------------------------- constant sources
+def _nrm(x):
+    return float(np.linalg.norm(x))
+
+
+def _lap_fft(u, L=1.0):
+    n = u.shape[0]
+    k = 2 * np.pi * np.fft.fftfreq(n, L / n)
+    kk = k[None, :] ** 2 + k[:, None] ** 2
+    return np.real(np.fft.ifft2(-kk * np.fft.fft2(u)))
+
+
+def pin_diffusion_source_pde(n=32, D=0.2, t=0.07, dt=1e-5, seed=13):
+    """u_t - D lap u = s (time central difference; Laplacian from numpy.fft) and u(0) = f."""
+    rng = np.random.default_rng(seed)
+    f = wl.mode_sum(wl.draw_modes(rng, 6, 5), n, n, 1.0, 1.0) + 0.3
+    src = wl.mode_sum(wl.draw_modes(rng, 6, 5), n, n, 1.0, 1.0) + 0.7
+    F, S = oracle.state_spectrum(f), oracle.state_spectrum(src)
+
+    def u(tt):
+        return np.real(oracle.idft2(oracle.diffusion_source_spectrum(F, S, D, tt, 1.0, 1.0)))
+    res = (u(t + dt) - u(t - dt)) / (2 * dt) - D * _lap_fft(u(t)) - src
+    return max(_nrm(res) / _nrm(src), rel(u(0.0), f))
+
+
+def pin_wave_source_pde(n=32, c=0.9, t=0.21, dt=2e-4, seed=14):
+    """u_tt - c^2 lap u = s, u(0) = f, u_t(0) = g, and v = u_t.
+
+    u_tt is the Richardson combination of central second differences at dt
+    and dt/2 (truncation O(dt^4)).
+    """
+    rng = np.random.default_rng(seed)
+    f = wl.mode_sum(wl.draw_modes(rng, 6, 3), n, n, 1.0, 1.0) + 0.2
+    g = wl.mode_sum(wl.draw_modes(rng, 6, 3), n, n, 1.0, 1.0) - 0.1
+    src = wl.mode_sum(wl.draw_modes(rng, 6, 3), n, n, 1.0, 1.0) + 0.4
+    F, G, S = (oracle.state_spectrum(x) for x in (f, g, src))
+
+    def uv(tt):
+        U, V = oracle.wave_source_spectrum(F, G, S, c, tt, 1.0, 1.0)
+        return np.real(oracle.idft2(U)), np.real(oracle.idft2(V))
+    u0, v0 = uv(t)
+
+    def d2(h):
+        return (uv(t + h)[0] - 2 * u0 + uv(t - h)[0]) / h**2
+    utt = (4 * d2(dt / 2) - d2(dt)) / 3
+    res = utt - c * c * _lap_fft(u0) - src
+    e1 = _nrm(res) / _nrm(src)
+    ut = (8 * (uv(t + dt / 2)[0] - uv(t - dt / 2)[0]) - (uv(t + dt)[0] - uv(t - dt)[0])) / (6 * dt)
+    e2 = rel(ut, v0)
+    a, b = uv(0.0)
+    return max(e1, e2, rel(a, f), rel(b, g))
+
+
 # name -> (function, bound)
 PINS = {
     "bruteforce": (pin_bruteforce, 1e-13),
@@ -288,4 +341,6 @@ PINS = {
     "wave_velocity_fd": (pin_wave_velocity_fd, 1e-6),
     "wave_invariants": (pin_wave_invariants, 1e-11),
     "sign_independence": (pin_sign_independence, 1e-13),
+    "diffusion_source_pde": (pin_diffusion_source_pde, 1e-6),
+    "wave_source_pde": (pin_wave_source_pde, 1e-5),
 }

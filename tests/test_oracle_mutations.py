@@ -88,6 +88,24 @@ def _dft1_sign_ignored(x, axis=-1, sign=-1):
     return _ORIG_DFT1(x, axis=axis, sign=+1)
 
 
+def _diffusion_source_gain_sign(F, S, D, t, lx, ly):
+    ny, nx = F.shape
+    lam = D * osolve.omega2(nx, ny, lx, ly)
+    gain = np.where(lam > 0, np.expm1(-lam * t) / np.where(lam > 0, lam, 1.0), t)
+    return F * np.exp(-lam * t) + S * gain
+
+
+def _wave_source_printed(F, G, S, c, t, lx, ly):
+    # the particular term subtracted inside the cosine but not added back
+    U, V = osolve.wave_spectrum(F, G, c, t, lx, ly)
+    ny, nx = F.shape
+    cw = c * np.sqrt(osolve.omega2(nx, ny, lx, ly))
+    cw2 = np.where(cw > 0, cw * cw, 1.0)
+    pu = np.where(cw > 0, -np.cos(cw * t) / cw2, 0.5 * t * t)
+    pv = np.where(cw > 0, np.sin(cw * t) / np.where(cw > 0, cw, 1.0), t)
+    return U + S * pu, V + S * pv
+
+
 _ORIG_DFT1 = odft.dft1
 _ORIG_WAVE = osolve.wave_spectrum
 
@@ -103,6 +121,8 @@ MUTANTS = {
     "idft2_unnormalised": [(osolve, "idft2", _idft2_unnormalised), (oracle, "idft2", _idft2_unnormalised)],
     "dft2_transposed": [(osolve, "dft2", _dft2_transposed), (oracle, "dft2", _dft2_transposed)],
     "dft1_sign_ignored": [(odft, "dft1", _dft1_sign_ignored), (oracle, "dft1", _dft1_sign_ignored)],
+    "diffusion_source_gain_sign": [(oracle, "diffusion_source_spectrum", _diffusion_source_gain_sign)],
+    "wave_source_printed_form": [(oracle, "wave_source_spectrum", _wave_source_printed)],
 }
 
 
