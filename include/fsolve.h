@@ -113,16 +113,34 @@ fs_status fs_state_destroy(fs_state state);
  * (same plan; v0 must be NULL iff the state was created without v0).  No
  * allocation; stream-ordered like fs_state_create. */
 fs_status fs_state_reset(fs_state state, const void *u0, const void *v0, fs_stream stream);
+/* fs_state_set_source: attach a time-independent source s (device [ny][nx] of
+ * the plan dtype, read during the call's stream work only) to a state; its
+ * forward transform S is kept beside U0/V0.  Every later advance of the state
+ * (per call, batched or served) then solves the forced problem of
+ * Eq. DiffusionIVPFS / Eq. WaveEquationFourierSpace with s != 0 mode by mode:
+ *   diffusion  U = U0 E + S (1 - E)/(D|w|^2), E = exp(-D|w|^2 t); U0 + S t at D|w|^2 = 0
+ *   wave       U = U0 cos th + V0 sin th/(c|w|) + S (1 - cos th)/(c|w|)^2,
+ *              V = -c|w| U0 sin th + V0 cos th + S sin th/(c|w|),  th = c|w|t;
+ *              U0 + V0 t + S t^2/2 and V0 + S t at w = 0
+ * (the particular term S/(c|w|)^2 that the printed Eq. OmegaNonZero leaves out
+ * of the non-zero modes is included).  s == NULL detaches the source (its
+ * spectrum buffer is kept for reuse).  Allocates the source spectrum on first
+ * use (FS_ERR_NOMEM / FS_ERR_CUDA on failure, state unchanged); a failed
+ * transform leaves the state without a source.  Stream-ordered like
+ * fs_state_reset. */
+fs_status fs_state_set_source(fs_state state, const void *s, fs_stream stream);
 
 /* fs_diffusion_advance: u(t) from a kept state, t absolute (>= 0) from the
  * state's initial data: inverse 2D DFT of U0 exp(-D|omega|^2 t)
- * (Eq. solCalorFourier).  u_out: device [ny][nx]. */
+ * (Eq. solCalorFourier), plus the source term when one is attached
+ * (fs_state_set_source).  u_out: device [ny][nx]. */
 fs_status fs_diffusion_advance(fs_state state, double D, double t, void *u_out, fs_stream stream);
 
 /* fs_wave_advance: u(t) (and v = u_t(t) when v_out != NULL) from a kept state:
  * U = U0 cos(c|omega|t) + V0 sin(c|omega|t)/(c|omega|), U = U0 + V0 t at
  * omega = 0 (Eq. OmegaZero/OmegaNonZero); V = -c|omega| U0 sin + V0 cos (the
- * first-order system, Eq. SystemOfODEsForWaveEquation). */
+ * first-order system, Eq. SystemOfODEsForWaveEquation); plus the source terms
+ * when a source is attached (fs_state_set_source). */
 fs_status fs_wave_advance(fs_state state, double c, double t, void *u_out, void *v_out,
                           fs_stream stream);
 

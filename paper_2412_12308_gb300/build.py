@@ -41,7 +41,7 @@ def _jobs():
                     # the units are called from kernels launched with <= 512 threads
                     out.append((src, [f"-DFS_T={t}", f"-DFS_E={e}", "-maxrregcount=128"],
                                 f"units_{t}_e{e}.o"))
-        elif name == "fs_pow2_f32.cu":
+        elif name in ("fs_pow2_f32.cu", "fs_pow2_src_f32.cu"):
             # its device units are called from kernels launched with <= 512 threads
             out.append((src, ["-maxrregcount=128"], name + ".o"))
         else:

@@ -5,6 +5,7 @@
     python -m paper_2412_12308_gb300.cases diffusion_batch --n 1024 --iters 5
     python -m paper_2412_12308_gb300.cases batch_mix --iters 5
     python -m paper_2412_12308_gb300.cases wave_snapshots --n 4096 --iters 5
+    python -m paper_2412_12308_gb300.cases wave_src_adv --n 4096 --iters 20
 
 Each case runs `--warmup` untimed repetitions, then `--iters` timed ones
 (CUDA events on the current stream) and prints one JSON line with the mean
@@ -66,6 +67,18 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
         def rep():
             fsolve.fs_diffusion_advance(state, 0.1, 0.37, out)
         algo = 2 * spec + spec + real
+    elif case in ("diffusion_src_adv", "wave_src_adv"):
+        # advance with a constant source: the column pass also reads the kept
+        # source spectrum
+        state = fsolve.fs_state_create(plan, fd)
+        fsolve.fs_state_set_source(state, fd)
+        if case == "diffusion_src_adv":
+            def rep():
+                fsolve.fs_diffusion_advance(state, 0.1, 0.37, out)
+        else:
+            def rep():
+                fsolve.fs_wave_advance(state, 1.0, 0.37, out)
+        algo = 3 * spec + spec + real
     elif case == "batch_mix":
         # 512 uneven problems (N in {64..2048}, all three operators) in one
         # persistent launch per repetition

@@ -506,11 +506,35 @@ fs_status fs_state_reset(fs_state s, const void *u0, const void *v0, fs_stream s
   return run(p, d, stream, "fs_state_reset");
 }
 
+fs_status fs_state_set_source(fs_state s, const void *src, fs_stream stream) {
+  if (!s) return set_error(FS_ERR_ARG, "fs_state_set_source: NULL state");
+  if (!src) {
+    s->has_s = false;
+    return FS_OK;
+  }
+  fs_plan p = s->plan;
+  if (!s->ss) {
+    cudaError_t e = alloc_dev(&s->ss, p->spec_bytes);
+    if (e != cudaSuccess) {
+      s->ss = nullptr;
+      return cuda_error(e, "fs_state_set_source: device allocation");
+    }
+  }
+  Desc d = base_desc(p);
+  d.op = OP_FORWARD;
+  d.in_u = src;
+  d.st_out_u = s->ss;
+  fs_status st = run(p, d, stream, "fs_state_set_source");
+  s->has_s = st == FS_OK;
+  return st;
+}
+
 fs_status fs_state_destroy(fs_state s) {
   if (!s) return FS_OK;
   cudaDeviceSynchronize();
   cudaFree(s->su);
   cudaFree(s->sv);
+  cudaFree(s->ss);
   delete s;
   return FS_OK;
 }
@@ -525,7 +549,12 @@ fs_status fs_diffusion_advance(fs_state s, double D, double t, void *u_out, fs_s
   d.st_u = s->su;
   d.out_u = u_out;
   d.p_dt = D * t;
+  d.p_d = D;
   d.p_t = t;
+  if (s->has_s) {
+    d.flags |= F_SOURCE;
+    d.st_s = s->ss;
+  }
   return run(p, d, stream, "fs_diffusion_advance");
 }
 
@@ -548,6 +577,10 @@ fs_status fs_wave_advance(fs_state s, double c, double t, void *u_out, void *v_o
   d.out_v = v_out;
   d.p_c = c;
   d.p_t = t;
+  if (s->has_s) {
+    d.flags |= F_SOURCE;
+    d.st_s = s->ss;
+  }
   return run(p, d, stream, "fs_wave_advance");
 }
 

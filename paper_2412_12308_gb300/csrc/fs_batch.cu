@@ -149,6 +149,7 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
         if (!(r.D >= 0.0) || !(r.t >= 0.0) || !std::isfinite(r.D * r.t))
           return set_error(FS_ERR_ARG, "fs_batch_submit: diffusion needs finite D >= 0, t >= 0");
         d.p_dt = r.D * r.t;
+        d.p_d = r.D;
         d.p_t = r.t;
         if (r.op == FS_OP_DIFFUSION) {
           if (!r.in_u) return set_error(FS_ERR_ARG, "fs_batch_submit: diffusion without input");
@@ -157,6 +158,10 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
         } else {
           d.op = OP_DIFF_ADV;
           d.st_u = r.state->su;
+          if (r.state->has_s) {
+            d.flags |= F_SOURCE;
+            d.st_s = r.state->ss;
+          }
         }
         break;
       case FS_OP_WAVE:
@@ -177,6 +182,10 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
           d.st_v = r.state->sv;
           d.flags = (r.state->has_v ? F_HAS_V0 : 0) | (r.out_v ? F_WANT_V : 0);
           d.out_v = r.out_v;
+          if (r.state->has_s) {
+            d.flags |= F_SOURCE;
+            d.st_s = r.state->ss;
+          }
         }
         break;
       default:

@@ -23,7 +23,8 @@ enum Op : int {
 
 enum Flags : int {
   F_HAS_V0 = 1,   // wave: an initial velocity field / spectrum is present
-  F_WANT_V = 2    // wave advance: also produce v = u_t
+  F_WANT_V = 2,   // wave advance: also produce v = u_t
+  F_SOURCE = 4    // advance: a kept constant-source spectrum st_s is added
 };
 
 // Unit kinds of the persistent batch kernel, in dependency order.
@@ -53,12 +54,14 @@ struct Desc {
   void *out_u, *out_v;        // real fields [ny][nx]
   void *work_u, *work_v;      // half-spectra [M+1][ny] (x-frequency major)
   const void *st_u, *st_v;    // kept spectra (advance ops)
+  const void *st_s;           // kept source spectrum (advance ops with F_SOURCE)
   void *st_out_u, *st_out_v;  // where OP_FORWARD keeps the spectra
   const void *tw_x, *tw_y;    // omega_nx^m (m < nx), omega_ny^m (m < ny)
   const void *wx2, *wy2;      // |omega_x|^2 (a <= M), |omega_y|^2 (b < ny); two-float or double
   const double *wx2d, *wy2d;  // the same in float64 (factor tables)
   void *fac;                  // diffusion per-axis factors: x part [M+1], y part [ny]
   double p_dt;                // D * t
+  double p_d;                 // diffusivity D (source gain of the diffusion advance)
   double p_c;                 // wave speed c
   double p_t;                 // time t
   double scale;               // 1 / (nx * ny)

@@ -50,7 +50,9 @@ struct fs_plan_s {
 struct fs_state_s {
   fs_plan plan;
   void *su, *sv;
+  void *ss;         // kept constant-source spectrum (nullptr: no source)
   bool has_v;
+  bool has_s;       // the source is applied by advances
 };
 
 namespace fs {

@@ -249,6 +249,14 @@ struct Launch {
     return launch(k, d.n_row_units * fields, row_threads(d), row_smem(d), d, s, PC_R2C);
   }
   static cudaError_t cols(const Desc &d, cudaStream_t s) {
+    // advances with a constant source: their own instantiations
+    if (d.flags & F_SOURCE) {
+      PassKernel k = nullptr;
+      if (sizeof(T) == 4 && d.rp_col.e == 16 && p2_col_ok(d.ny) && d.cols_per_unit == p2_col_cnt(d.ny))
+        k = p2_cols_f32(d.ny, col_two_fields(d));
+      if (!k) k = pass_kernels<T>(d.rp_col.e).cols;
+      return launch(k, d.n_col_units, col_threads(d), col_smem(d), d, s, PC_COL);
+    }
     // measured variant: split-BF16 tensor-core first stage (advances only)
     if (sizeof(T) == 4 && tc_variant_requested() && !col_two_fields(d) && d.rp_col.e == 16 &&
         (d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV)) {

@@ -28,12 +28,16 @@ __device__ bool p2_unit_c2r(const Desc &d, int unit, int cnt, cx<float> *sm, con
                             bool sh);
 __device__ bool p2_unit_col1(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu, cx<float> *wv,
                              bool sh);
+// columns of an advance with a constant source, one or two fields
+__device__ bool p2_unit_cols(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu, cx<float> *wv,
+                             bool sh);
 
 // Kernel lookup (nullptr when not specialised).
 PassKernel p2_r2c_f32(int M);
 PassKernel p2_c2r_f32(int M);
 PassKernel p2_col1_f32(int L);
 PassKernel p2_col2_f32(int L);
+PassKernel p2_cols_f32(int L, bool two);  // advances with a constant source
 // TMA-staged persistent column kernel (single field) and its shared memory.
 PassKernel p2_col_tma_f32(int L);
 // Split-BF16 tensor-core first stage (measured variant, FS_COLUMN_VARIANT=bf16x3).

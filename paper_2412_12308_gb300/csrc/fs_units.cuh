@@ -188,6 +188,27 @@ __device__ __forceinline__ void col_op_single(const Desc &d, const OpCtx<T> &o, 
   }
 }
 
+// Single-field advance with a constant source; `sc` is the column of the kept
+// source spectrum.  Diffusion, or the wave without initial velocity and
+// without v output.
+template <typename T, int E>
+__device__ __forceinline__ void col_op_source(const Desc &d, const OpCtx<T> &o, int t, int Tseg,
+                                              cx<T> (&u)[E], const cx<T> *sc) {
+  if (d.op == OP_DIFF_ADV) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const DiffS<T> f = diff_src_mult(o, d, t + Tseg * s);
+      u[s] = conj(f.m * u[s] + f.g * ldg_cg(sc + t + Tseg * s));
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const WaveS<T> f = wave_src_mult(o, d, t + Tseg * s);
+      u[s] = conj(f.cu * u[s] + f.pu * ldg_cg(sc + t + Tseg * s));
+    }
+  }
+}
+
 // TWO: a second field (initial velocity in, or velocity out) is carried;
 // the single-field variant holds one register tile only.
 __host__ __device__ inline bool col_two_fields(const Desc &d) {
@@ -198,7 +219,9 @@ __host__ __device__ inline bool col_two_fields(const Desc &d) {
 }
 
 // LC, CC: compile-time column length and columns per unit (0 = from d / cnt_rt).
-template <typename T, int E, bool TWO, int LC = 0, int CC = 0>
+// SRC: advance ops with a constant source (F_SOURCE); a separate instantiation
+// so that the source-free kernels keep their register allocation.
+template <typename T, int E, bool TWO, int LC = 0, int CC = 0, bool SRC = false>
 __device__ __forceinline__ void unit_col_t(const Desc &d, int unit, int cnt_rt, cx<T> *sm, cx<T> *wu,
                                            cx<T> *wv, bool sh) {
   const int L = LC ? LC : d.ny, M = d.M, Tseg = L / E;
@@ -275,7 +298,20 @@ __device__ __forceinline__ void unit_col_t(const Desc &d, int unit, int cnt_rt, 
   // inverse transform by conjugation
   if (active) {
     const OpCtx<T> o = op_ctx<T>(d, a);
-    if (op == OP_POISSON || op == OP_DIFFUSION || op == OP_DIFF_ADV || !TWO) {
+    if constexpr (SRC) {  // advance ops only (the host sets F_SOURCE on advances)
+      const cx<T> *sc = reinterpret_cast<const cx<T> *>(d.st_s) + cofs;
+      if (op == OP_DIFF_ADV || !TWO) {
+        col_op_source<T, E>(d, o, t, Tseg, u, sc);
+      } else if constexpr (TWO) {
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+          const WaveS<T> f = wave_src_mult(o, d, t + Tseg * s);
+          const cx<T> u0 = u[s], v0 = w[s], s0 = ldg_cg(sc + t + Tseg * s);
+          u[s] = conj(f.cu * u0 + f.su * v0 + f.pu * s0);
+          w[s] = conj(f.sv * u0 + f.cu * v0 + f.su * s0);
+        }
+      }
+    } else if (op == OP_POISSON || op == OP_DIFFUSION || op == OP_DIFF_ADV || !TWO) {
       col_op_single<T, E>(d, o, t, Tseg, u);
     } else if constexpr (TWO) {  // wave carrying a velocity field
 #pragma unroll
@@ -370,7 +406,8 @@ __device__ __forceinline__ void kbody_c2r(const Desc &d, cx<T> *sm) {
   __global__ void k_r2c_##T##_##E(const Desc d);                           \
   __global__ void k_c2r_##T##_##E(const Desc d);                           \
   __global__ void k_col1_##T##_##E(const Desc d);                          \
-  __global__ void k_col2_##T##_##E(const Desc d);
+  __global__ void k_col2_##T##_##E(const Desc d);                          \
+  __global__ void k_cols_##T##_##E(const Desc d);
 
 #define FS_UNIT_DECL(T, E)                                                                     \
   FS_KERNEL_DECL(T, E)                                                                         \
@@ -382,6 +419,8 @@ __device__ __forceinline__ void kbody_c2r(const Desc &d, cx<T> *sm) {
   __device__ __noinline__ void unit_col_##T##_##E(const Desc &d, int unit, int cnt, cx<T> *sm, \
                                                   cx<T> *wu, cx<T> *wv, bool sh);              \
   __device__ __noinline__ void unit_col2_##T##_##E(const Desc &d, int unit, int cnt, cx<T> *sm,\
+                                                   cx<T> *wu, cx<T> *wv, bool sh);             \
+  __device__ __noinline__ void unit_cols_##T##_##E(const Desc &d, int unit, int cnt, cx<T> *sm,\
                                                    cx<T> *wu, cx<T> *wv, bool sh);
 
 #define FS_UNIT_DEF(T, E)                                                                       \
@@ -402,6 +441,10 @@ __device__ __forceinline__ void kbody_c2r(const Desc &d, cx<T> *sm) {
                                                    cx<T> *wu, cx<T> *wv, bool sh) {             \
     unit_col_t<T, E, true>(d, unit, cnt, sm, wu, wv, sh);                                       \
   }                                                                                             \
+  __device__ __noinline__ void unit_cols_##T##_##E(const Desc &d, int unit, int cnt, cx<T> *sm, \
+                                                   cx<T> *wu, cx<T> *wv, bool sh) {             \
+    unit_col_t<T, E, true, 0, 0, true>(d, unit, cnt, sm, wu, wv, sh);                           \
+  }                                                                                             \
   __global__ void __launch_bounds__(512) k_r2c_##T##_##E(const Desc d) {                        \
     extern __shared__ __align__(16) unsigned char fs_smem[];                                    \
     kbody_r2c<T, E>(d, reinterpret_cast<cx<T> *>(fs_smem));                                     \
@@ -421,6 +464,13 @@ __device__ __forceinline__ void kbody_c2r(const Desc &d, cx<T> *sm) {
     unit_col_t<T, E, true>(d, blockIdx.x, d.cols_per_unit, reinterpret_cast<cx<T> *>(fs_smem),  \
                            reinterpret_cast<cx<T> *>(d.work_u),                                 \
                            reinterpret_cast<cx<T> *>(d.work_v), false);                         \
+  }                                                                                             \
+  __global__ void __launch_bounds__(512) k_cols_##T##_##E(const Desc d) {                       \
+    extern __shared__ __align__(16) unsigned char fs_smem[];                                    \
+    unit_col_t<T, E, true, 0, 0, true>(d, blockIdx.x, d.cols_per_unit,                          \
+                                       reinterpret_cast<cx<T> *>(fs_smem),                      \
+                                       reinterpret_cast<cx<T> *>(d.work_u),                     \
+                                       reinterpret_cast<cx<T> *>(d.work_v), false);             \
   }
 
 // Register tiles: FP32 uses up to 16/24/20 elements per thread for the
@@ -466,11 +516,12 @@ FS_FOR_EACH_E_double(FS_UNIT_DECL)
 
 // Host-side kernel lookup by register tile.
 struct PassKernels {
-  PassKernel r2c, c2r, col1, col2;
+  PassKernel r2c, c2r, col1, col2, cols;
 };
-#define FS_PK_CASE(T, E) \
-  case E:                \
-    return PassKernels{k_r2c_##T##_##E, k_c2r_##T##_##E, k_col1_##T##_##E, k_col2_##T##_##E};
+#define FS_PK_CASE(T, E)                                                                      \
+  case E:                                                                                     \
+    return PassKernels{k_r2c_##T##_##E, k_c2r_##T##_##E, k_col1_##T##_##E, k_col2_##T##_##E, \
+                       k_cols_##T##_##E};
 template <typename T>
 inline PassKernels pass_kernels(int e);
 template <>
@@ -504,6 +555,13 @@ __device__ __forceinline__ bool pow2_col1(const Desc &d, int unit, int cnt, cx<f
 __device__ __forceinline__ bool pow2_col1(const Desc &, int, int, cx<double> *, cx<double> *, cx<double> *, bool) {
   return false;
 }
+__device__ __forceinline__ bool pow2_cols(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu,
+                                          cx<float> *wv, bool sh) {
+  return p2_unit_cols(d, unit, cnt, sm, wu, wv, sh);
+}
+__device__ __forceinline__ bool pow2_cols(const Desc &, int, int, cx<double> *, cx<double> *, cx<double> *, bool) {
+  return false;
+}
 
 template <typename T>
 struct Units;
@@ -522,7 +580,10 @@ struct Units;
     }                                                                                           \
     static __device__ __forceinline__ void col(const Desc &d, int unit, int cnt, cx<T> *sm,     \
                                                cx<T> *wu, cx<T> *wv, bool sh) {                 \
-      if (col_two_fields(d)) {                                                                  \
+      if (d.flags & F_SOURCE) {                                                                 \
+        if (pow2_cols(d, unit, cnt, sm, wu, wv, sh)) return;                                    \
+        FS_E_SWITCH_##T(d.rp_col.e, unit_cols, d, unit, cnt, sm, wu, wv, sh)                    \
+      } else if (col_two_fields(d)) {                                                           \
         FS_E_SWITCH_##T(d.rp_col.e, unit_col2, d, unit, cnt, sm, wu, wv, sh)                    \
       } else {                                                                                  \
         if (pow2_col1(d, unit, cnt, sm, wu, wv, sh)) return;                                    \

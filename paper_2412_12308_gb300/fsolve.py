@@ -56,6 +56,7 @@ _SIGS = {
     "fs_state_create": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "fs_state_destroy": (ctypes.c_int, [_vp]),
     "fs_state_reset": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "fs_state_set_source": (ctypes.c_int, [_vp, _vp, _vp]),
     "fs_diffusion_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
     "fs_batch_submit": (ctypes.c_int, [ctypes.POINTER(FsRequest), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
@@ -200,6 +201,12 @@ def fs_state_destroy(state):
 def fs_state_reset(state, u0, v0=None, stream=None):
     load()
     _check(_lib.fs_state_reset(state, _ptr(u0), _ptr(v0), _stream(stream)), "fs_state_reset")
+
+
+def fs_state_set_source(state, s, stream=None):
+    """Attach a constant source field (None detaches it) to a kept state."""
+    load()
+    _check(_lib.fs_state_set_source(state, _ptr(s), _stream(stream)), "fs_state_set_source")
 
 
 def fs_diffusion_advance(state, D, t, u_out, stream=None):

@@ -100,6 +100,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.fs_wave_advance(None, 1.0, 0.0, None, None, None) == -1
     assert lib.fs_plan_destroy(None) == 0
     assert lib.fs_state_destroy(None) == 0
+    assert lib.fs_state_set_source(None, None, None) == -1
 
 
 def test_binding_raises_with_message(lib):
