@@ -29,6 +29,7 @@ __all__ = [
     "batch_mix",
     "ServeRequest",
     "serve_stream",
+    "OrbitSource",
 ]
 
 
@@ -224,3 +225,42 @@ def serve_stream(rate_per_s, seed=12312, count=20000, nmin=128, nmax=8192, follo
             req.followup_delay_s = float(rng.exponential(followup_mean_s))
         out.append(req)
     return out
+
+
+# --------------------------------------------------------------------------
+# Time-dependent source of the wave example (Sec. III.C, example with source)
+# --------------------------------------------------------------------------
+
+@dataclass
+class OrbitSource:
+    """s(t, x, y) = A exp(-|x - x0(t)|^2 / sigma^2) cos(gamma t), with the
+    centre on a circle: x0(t) = radius (cos(Omega t), sin(Omega t)).
+
+    The paper's parameters: A = 1, sigma = 0.1, Omega = 5, gamma = 10 on
+    [-2, 2]^2.  The orbit radius is not stated; radius = 1 is our reading.
+    The distance is the minimum image on the periodic domain (images beyond
+    it contribute below e^-100 for these widths).  Grid x_j = x_min + j Lx/Nx.
+    """
+
+    A: float = 1.0
+    sigma: float = 0.1
+    radius: float = 1.0
+    Omega: float = 5.0
+    gamma: float = 10.0
+    x_min: float = -2.0
+    y_min: float = -2.0
+
+    def centre(self, t):
+        return self.radius * math.cos(self.Omega * t), self.radius * math.sin(self.Omega * t)
+
+    def field(self, t, nx, ny, lx, ly):
+        """The source sampled on the [ny][nx] grid at time t (float64)."""
+        cx, cy = self.centre(t)
+        x, y = grid(nx, ny, lx, ly, self.x_min, self.y_min)
+        dx = x - cx
+        dx -= lx * np.round(dx / lx)
+        dy = y - cy
+        dy -= ly * np.round(dy / ly)
+        r2 = dy[:, None] ** 2 + dx[None, :] ** 2
+        return self.A * math.cos(self.gamma * t) * np.exp(-r2 / self.sigma**2)
+

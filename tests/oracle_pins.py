@@ -320,6 +320,72 @@ def pin_wave_source_pde(n=32, c=0.9, t=0.21, dt=2e-4, seed=14):
     return max(e1, e2, rel(a, f), rel(b, g))
 
 
+# ----------------------------------------------------------------------- RK4
+def pin_rk4_propagator(nx=8, ny=6, lx=1.3, ly=0.9, c=1.1, dt=0.06, seed=15):
+    """One RK4 step of the free oscillator is the degree-4 Taylor polynomial of
+    exp(dt A), A = [[0, 1], [-w^2, 0]]; with A^2 = -w^2 I it is
+    a I + b A, a = 1 - z^2/2 + z^4/24, b = dt (1 - z^2/6), z = dt w."""
+    rng = np.random.default_rng(seed)
+    F = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+    G = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+    U, V = oracle.wave_rk4_spectrum(F, G, None, c, 0.0, dt, 1, lx, ly)
+    w2 = c * c * oracle.omega2(nx, ny, lx, ly)
+    z2 = dt * dt * w2
+    a = 1.0 - z2 / 2.0 + z2 * z2 / 24.0
+    b = dt * (1.0 - z2 / 6.0)
+    return max(rel(U, a * F + b * G), rel(V, a * G - w2 * b * F))
+
+
+def _const_gauss(n, L):
+    src = wl.OrbitSource(A=1.0, sigma=0.5, radius=0.3, Omega=0.0, gamma=0.0)
+    return src.field(0.0, n, n, L, L)
+
+
+def pin_rk4_constant_source_order(n=16, L=4.0, c=1.0, T=0.5, seed=16):
+    """Constant source: RK4 converges to solve.wave_source_spectrum with
+    order 4 (errors at dt = 0.01 and 0.005 in ratio ~16) and is within
+    1.5e-6 of it at dt = 0.005."""
+    rng = np.random.default_rng(seed)
+    F = oracle.state_spectrum(rng.standard_normal((n, n)))
+    G = oracle.state_spectrum(rng.standard_normal((n, n)))
+    s = _const_gauss(n, L)
+    Ue, _ = oracle.wave_source_spectrum(F, G, oracle.state_spectrum(s), c, T, L, L)
+    errs = []
+    for steps in (50, 100):
+        U, _ = oracle.wave_rk4_spectrum(F, G, lambda t: s, c, 0.0, T / steps, steps, L, L)
+        errs.append(rel(U, Ue))
+    order = math.log2(errs[0] / errs[1])
+    return max(abs(order - 4.0), errs[1] / 1e-5)
+
+
+def _orbit_mean(n, dt, T, L=4.0):
+    src = wl.OrbitSource()
+    steps = int(round(T / dt))
+    U, _ = oracle.wave_rk4_spectrum(np.zeros((n, n)), None, lambda t: src.field(t, n, n, L, L), 1.0, 0.0, dt,
+                                    steps, L, L)
+    return U[0, 0].real / (n * n)
+
+
+def pin_rk4_orbit_self_convergence(n=64, T=1.0):
+    """The paper's example with an orbiting source (A = 1, sigma = 0.1, Omega = 5,
+    gamma = 10 on [-2, 2]^2, dt = h/4 for N = 64, 128, 256): the means u1, u2,
+    u3 at dt, dt/2, dt/4 self-converge with (u2 - u1)/(u3 - u2) ~ 2^4
+    (tests/golden/paper_facts.txt); also the mean mode u'' = mean(s) has the
+    exact solution A pi sigma^2/L^2 (1 - cos(gamma t))/gamma^2 (the grid sum
+    of the Gaussian equals pi sigma^2/h^2 to ~1e-11 at N = 64), and u3 is
+    within twice the Richardson estimate |u3 - u2|/15 of it."""
+    from tests.golden import load_facts
+
+    dts = [0.25 * 4.0 / N for N in (64, 128, 256)]
+    u1, u2, u3 = (_orbit_mean(n, dt, T) for dt in dts)
+    factor = (u2 - u1) / (u3 - u2)
+    want = load_facts()["rk4_self_convergence_factor"]
+    src = wl.OrbitSource()
+    exact = src.A * math.pi * src.sigma**2 / 16.0 * (1.0 - math.cos(src.gamma * T)) / src.gamma**2
+    richardson = abs(u3 - u2) / 15.0
+    return max(abs(factor - want) / want, 0.1 * abs(u3 - exact) / (2.0 * richardson))
+
+
 # name -> (function, bound)
 PINS = {
     "bruteforce": (pin_bruteforce, 1e-13),
@@ -343,4 +409,7 @@ PINS = {
     "sign_independence": (pin_sign_independence, 1e-13),
     "diffusion_source_pde": (pin_diffusion_source_pde, 1e-6),
     "wave_source_pde": (pin_wave_source_pde, 1e-5),
+    "rk4_propagator": (pin_rk4_propagator, 1e-13),
+    "rk4_constant_source_order": (pin_rk4_constant_source_order, 0.15),
+    "rk4_orbit_self_convergence": (pin_rk4_orbit_self_convergence, 0.1),
 }

@@ -106,6 +106,33 @@ def _wave_source_printed(F, G, S, c, t, lx, ly):
     return U + S * pu, V + S * pv
 
 
+def _rk4_variant(weights=(1, 2, 2, 1), src_stage=("start", "mid", "mid", "end"), k2_step=0.5):
+    import oracle.rk4 as ork
+
+    def fn(F, G, source, c, t0, dt, nsteps, lx, ly, sign=-1):
+        F = np.asarray(F, dtype=np.complex128)
+        ny, nx = F.shape
+        w2 = float(c) ** 2 * osolve.omega2(nx, ny, lx, ly)
+        U = F.copy()
+        V = np.zeros_like(U) if G is None else np.asarray(G, dtype=np.complex128).copy()
+
+        def S(t):
+            return np.zeros_like(U) if source is None else ork.dft2(np.asarray(source(t), float), sign=sign)
+        for k in range(int(nsteps)):
+            t = t0 + k * dt
+            at = {"start": S(t), "mid": S(t + dt / 2), "end": S(t + dt)}
+            s1, s2, s3, s4 = (at[x] for x in src_stage)
+            k1u, k1v = V, -w2 * U + s1
+            k2u, k2v = V + k2_step * dt * k1v, -w2 * (U + k2_step * dt * k1u) + s2
+            k3u, k3v = V + 0.5 * dt * k2v, -w2 * (U + 0.5 * dt * k2u) + s3
+            k4u, k4v = V + dt * k3v, -w2 * (U + dt * k3u) + s4
+            a, b, cc, d = weights
+            U = U + dt / 6 * (a * k1u + b * k2u + cc * k3u + d * k4u)
+            V = V + dt / 6 * (a * k1v + b * k2v + cc * k3v + d * k4v)
+        return U, V
+    return fn
+
+
 _ORIG_DFT1 = odft.dft1
 _ORIG_WAVE = osolve.wave_spectrum
 
@@ -123,6 +150,10 @@ MUTANTS = {
     "dft1_sign_ignored": [(odft, "dft1", _dft1_sign_ignored), (oracle, "dft1", _dft1_sign_ignored)],
     "diffusion_source_gain_sign": [(oracle, "diffusion_source_spectrum", _diffusion_source_gain_sign)],
     "wave_source_printed_form": [(oracle, "wave_source_spectrum", _wave_source_printed)],
+    "rk4_weights": [(oracle, "wave_rk4_spectrum", _rk4_variant(weights=(1, 1, 2, 2)))],
+    "rk4_source_at_step_start": [(oracle, "wave_rk4_spectrum",
+                                  _rk4_variant(src_stage=("start", "start", "start", "start")))],
+    "rk4_k2_full_step": [(oracle, "wave_rk4_spectrum", _rk4_variant(k2_step=1.0))],
 }
 
 
