@@ -144,6 +144,52 @@ fs_status fs_diffusion_advance(fs_state state, double D, double t, void *u_out, 
 fs_status fs_wave_advance(fs_state state, double c, double t, void *u_out, void *v_out,
                           fs_stream stream);
 
+/* ---------------------------------------------------------------- RK4, moving source
+ * The wave equation u_tt = c^2 lap u + s(t, x, y) with the orbiting Gaussian
+ * source of Sec. III.C (example with source):
+ *   s = A exp(-|x - x0(t)|^2 / sigma^2) cos(gamma t),
+ *   x0(t) = radius (cos(Omega t), sin(Omega t)),
+ * |x - x0| the minimum-image distance on the periodic domain, grid points
+ * x_j = x_min + j Lx/nx, y_i = y_min + i Ly/ny.  Every mode of the half
+ * spectrum is advanced with the classical fourth-order Runge-Kutta method on
+ * the first-order system of Eq. SystemOfODEsForWaveEquation,
+ *   dU/dt = V,  dV/dt = -c^2 |omega|^2 U + S(t),
+ * S(t) the forward 2D DFT of the source sampled on the grid, evaluated at
+ * t_k, t_k + dt/2 and t_k + dt for the step from t_k.  The paper's example:
+ * A = 1, sigma = 0.1, Omega = 5, gamma = 10 on [-2, 2]^2, dt = h/4.
+ */
+typedef struct fs_rk4_s *fs_rk4;
+typedef struct {
+  double A, sigma, radius, Omega, gamma; /* sigma > 0; all finite */
+  double x_min, y_min;                   /* grid origin */
+} fs_orbit_source;
+
+/* fs_rk4_create: integrator at time t0 from u(t0) = u0 and u_t(t0) = v0
+ * (device [ny][nx] of the plan dtype, read during the call's stream work;
+ * NULL = zero field).  Allocates five half spectra (U, V, S(t) and two
+ * row-transform buffers) and a step table; FS_ERR_ARG on a NULL plan/src/out,
+ * c <= 0, non-finite or sigma <= 0 parameters; FS_ERR_CUDA on allocation or
+ * launch failure (nothing is leaked).  The plan must outlive the integrator. */
+fs_status fs_rk4_create(fs_plan plan, double c, const fs_orbit_source *src, const void *u0,
+                        const void *v0, double t0, fs_stream stream, fs_rk4 *out);
+/* fs_rk4_step: nsteps RK4 steps of size dt (> 0, finite; nsteps >= 0), stream
+ * ordered.  The per-step source table is uploaded from pageable memory (the
+ * call waits for earlier work on the stream), then a CUDA graph of the
+ * 2 x nsteps launches is replayed (captured on first use for each
+ * (nsteps, dt)).  Explicit RK4 is stable for dt c |omega|_max <= 2.8 (the
+ * paper's dt = h/4 gives ~1.1); larger steps are not rejected. */
+fs_status fs_rk4_step(fs_rk4 rk, double dt, int nsteps, fs_stream stream);
+/* fs_rk4_output: u (and u_t when v_out != NULL) at the current time, device
+ * [ny][nx]: the inverse 2D DFT of U (and V). */
+fs_status fs_rk4_output(fs_rk4 rk, void *u_out, void *v_out, fs_stream stream);
+/* fs_rk4_mean: the grid mean of u at the current time (U's zero mode divided
+ * by nx ny); synchronises the stream. */
+fs_status fs_rk4_mean(fs_rk4 rk, double *mean_u, fs_stream stream);
+/* fs_rk4_time: the integrator's current time t0 + (steps taken) dt. */
+fs_status fs_rk4_time(fs_rk4 rk, double *t);
+/* fs_rk4_destroy: synchronises the device, frees everything (NULL is a no-op). */
+fs_status fs_rk4_destroy(fs_rk4 rk);
+
 /* ---------------------------------------------------------------- batches
  * A request of a batch.  op: one of FS_OP_*.  The solve ops read `in_u`
  * (and `in_v` for FS_OP_WAVE, may be NULL) and write `out_u`; the advance ops

@@ -79,6 +79,23 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
             def rep():
                 fsolve.fs_wave_advance(state, 1.0, 0.37, out)
         algo = 3 * spec + spec + real
+    elif case == "wave_rk4":
+        # RK4 with the orbiting source (A = 1, sigma = 0.1, Omega = 5, gamma = 10,
+        # [-2, 2]^2, dt = h/4): one repetition = `rk4_steps` steps (one graph
+        # replay); N = 256 with 640 steps is the paper's run to t = 2.5
+        from .workloads import OrbitSource
+
+        plan_rk = fs.fs_plan_create(n, n, 4.0, 4.0, dtype)
+        rk = fs.fs_rk4_create(plan_rk, 1.0, OrbitSource())
+        dt = 0.25 * 4.0 / n
+        nst = 640 if n <= 256 else 20
+
+        def rep():
+            fsolve.fs_rk4_step(rk, dt, nst)
+        algo = nst * 10 * spec  # rows write 2 spectra; columns read 5, write 3
+        extra["rk4_steps_per_rep"] = nst
+        extra["dt"] = dt
+        extra["_rk4"] = (rk, plan_rk)
     elif case == "batch_mix":
         # 512 uneven problems (N in {64..2048}, all three operators) in one
         # persistent launch per repetition
@@ -140,7 +157,11 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
     res = {"case": case, "n": n, "dtype": dtype, "iters": iters, "ms_per_rep": round(ms, 5),
            "algorithmic_bytes": algo, "algorithmic_GBps": round(algo / (ms / 1e3) / 1e9, 1)}
     cleanup = extra.pop("_cleanup", None)
+    rk4 = extra.pop("_rk4", None)
     res.update(extra)
+    if rk4 is not None:
+        res["us_per_rk4_step"] = round(1e3 * ms / extra["rk4_steps_per_rep"], 3)
+        res["rk4_steps_per_s"] = round(extra["rk4_steps_per_rep"] / (ms / 1e3), 1)
     if "solves_per_rep" in extra:
         res["solves_per_s"] = round(extra["solves_per_rep"] / (ms / 1e3), 1)
     if profile:
@@ -153,6 +174,9 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
         res["per_kernel_us"] = {k: round(1e3 * v[1] / v[0], 3) for k, v in prof.items() if v[0]}
     if state is not None:
         fsolve.fs_state_destroy(state)
+    if rk4 is not None:
+        fsolve.fs_rk4_destroy(rk4[0])
+        fsolve.fs_plan_destroy(rk4[1])
     for h in (cleanup or {}).values():
         fsolve.fs_plan_destroy(h)
     fsolve.fs_plan_destroy(plan)

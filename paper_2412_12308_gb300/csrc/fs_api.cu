@@ -408,6 +408,24 @@ static fs_status run(const fs_plan_s *p, const Desc &d, fs_stream stream, const 
   return FS_OK;
 }
 
+namespace fs {
+fs_status forward_into(const fs_plan_s *p, const void *u0, const void *v0, void *su, void *sv,
+                       fs_stream stream, const char *what) {
+  if (v0 && !p->standalone_small) {
+    fs_status st = ensure_work_v(const_cast<fs_plan_s *>(p));
+    if (st != FS_OK) return st;
+  }
+  Desc d = base_desc(p);
+  d.op = OP_FORWARD;
+  d.flags = v0 ? F_HAS_V0 : 0;
+  d.in_u = u0;
+  d.in_v = v0;
+  d.st_out_u = su;
+  d.st_out_v = sv;
+  return run(p, d, stream, what);
+}
+}  // namespace fs
+
 extern "C" {
 
 fs_status fs_poisson_solve(fs_plan p, const void *f, void *u, fs_stream stream) {

@@ -60,5 +60,9 @@ namespace fs {
 bool plan_geometry(int nx, int ny, bool f64, RadixPlan *rr, RadixPlan *rc, TileConfig *tc);
 // Descriptor with the plan's geometry, tables and tile shapes filled in.
 Desc base_desc(const fs_plan_s *p);
+// Forward 2D DFT of u0 (and v0 when not NULL) into the half spectra su (sv),
+// stream-ordered; the plan's own path (single CTA or three passes).
+fs_status forward_into(const fs_plan_s *p, const void *u0, const void *v0, void *su, void *sv,
+                       fs_stream stream, const char *what);
 size_t fac_bytes(const fs_plan_s *p);
 }  // namespace fs

@@ -15,6 +15,7 @@
 // run (the column pass streams whole columns) and makes the row passes write
 // and read runs of `rows_per_unit` consecutive y values per frequency.
 #pragma once
+#include <type_traits>
 #include "fs_ops.cuh"
 #include "fs_pow2.h"
 
@@ -56,9 +57,12 @@ __device__ __forceinline__ cx<T> zero_cx() {
 // transform Z, X_a = (Z_a + conj Z_{M-a})/2 + w^a (Z_a - conj Z_{M-a})/(2i),
 // w = e^{-2 pi i/nx}; X_0 and X_M are real.
 // MC, CC: compile-time row length M and rows per tile (0 = read from d / cnt_rt).
-template <typename T, int E, int MC = 0, int CC = 0>
+// GEN: when not void, the real input is synthesised instead of loaded:
+// gen->pair(y, x) returns (f(x, y), f(x + 1, y)) and `in` is unused.
+template <typename T, int E, int MC = 0, int CC = 0, typename GEN = void>
 __device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt_rt, cx<T> *sm,
-                                               const T *__restrict__ in, cx<T> *spec) {
+                                               const T *__restrict__ in, cx<T> *spec,
+                                               const GEN *gen = nullptr) {
   const int M = MC ? MC : d.M, ny = d.ny, Tseg = M / E;
   const int cnt = CC ? CC : cnt_rt;
   const int tid = threadIdx.x;
@@ -69,9 +73,14 @@ __device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt_
   const cx<T> *tw = reinterpret_cast<const cx<T> *>(d.tw_x);
   cx<T> v[E];
   if (active) {
-    const cx<T> *row = reinterpret_cast<const cx<T> *>(in + (size_t)y * d.nx);
+    if constexpr (std::is_void<GEN>::value) {
+      const cx<T> *row = reinterpret_cast<const cx<T> *>(in + (size_t)y * d.nx);
 #pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = ldg_cg(row + t + Tseg * s);
+      for (int s = 0; s < E; ++s) v[s] = ldg_cg(row + t + Tseg * s);
+    } else {
+#pragma unroll
+      for (int s = 0; s < E; ++s) v[s] = gen->pair(y, 2 * (t + Tseg * s));
+    }
   } else {
 #pragma unroll
     for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();

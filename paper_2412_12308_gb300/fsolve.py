@@ -40,6 +40,14 @@ class FsRequest(ctypes.Structure):
                 ("t", ctypes.c_double), ("keep", ctypes.c_int), ("parent", ctypes.c_uint64)]
 
 
+class FsOrbitSource(ctypes.Structure):
+    """fs_orbit_source of include/fsolve.h."""
+
+    _fields_ = [("A", ctypes.c_double), ("sigma", ctypes.c_double), ("radius", ctypes.c_double),
+                ("Omega", ctypes.c_double), ("gamma", ctypes.c_double), ("x_min", ctypes.c_double),
+                ("y_min", ctypes.c_double)]
+
+
 # Entry points declared in include/fsolve.h: name -> (restype, argtypes)
 _SIGS = {
     "fs_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -59,6 +67,13 @@ _SIGS = {
     "fs_state_set_source": (ctypes.c_int, [_vp, _vp, _vp]),
     "fs_diffusion_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
+    "fs_rk4_create": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.POINTER(FsOrbitSource), _vp, _vp,
+                                     ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
+    "fs_rk4_step": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp]),
+    "fs_rk4_output": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "fs_rk4_mean": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "fs_rk4_time": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "fs_rk4_destroy": (ctypes.c_int, [_vp]),
     "fs_batch_submit": (ctypes.c_int, [ctypes.POINTER(FsRequest), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                        _vp]),
     "fs_batch_wait": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
@@ -207,6 +222,48 @@ def fs_state_set_source(state, s, stream=None):
     """Attach a constant source field (None detaches it) to a kept state."""
     load()
     _check(_lib.fs_state_set_source(state, _ptr(s), _stream(stream)), "fs_state_set_source")
+
+
+def fs_rk4_create(plan, c, src, u0=None, v0=None, t0=0.0, stream=None):
+    """RK4 integrator of the wave equation with an orbiting source.
+
+    `src` has the fields of fs_orbit_source (e.g. workloads.OrbitSource)."""
+    load()
+    s = FsOrbitSource(float(src.A), float(src.sigma), float(src.radius), float(src.Omega), float(src.gamma),
+                      float(src.x_min), float(src.y_min))
+    h = _vp()
+    _check(_lib.fs_rk4_create(plan, float(c), ctypes.byref(s), _ptr(u0), _ptr(v0), float(t0), _stream(stream),
+                              ctypes.byref(h)), "fs_rk4_create")
+    return h
+
+
+def fs_rk4_step(rk, dt, nsteps, stream=None):
+    load()
+    _check(_lib.fs_rk4_step(rk, float(dt), int(nsteps), _stream(stream)), "fs_rk4_step")
+
+
+def fs_rk4_output(rk, u_out, v_out=None, stream=None):
+    load()
+    _check(_lib.fs_rk4_output(rk, _ptr(u_out), _ptr(v_out), _stream(stream)), "fs_rk4_output")
+
+
+def fs_rk4_mean(rk, stream=None):
+    load()
+    m = ctypes.c_double()
+    _check(_lib.fs_rk4_mean(rk, ctypes.byref(m), _stream(stream)), "fs_rk4_mean")
+    return m.value
+
+
+def fs_rk4_time(rk):
+    load()
+    t = ctypes.c_double()
+    _check(_lib.fs_rk4_time(rk, ctypes.byref(t)), "fs_rk4_time")
+    return t.value
+
+
+def fs_rk4_destroy(rk):
+    load()
+    _check(_lib.fs_rk4_destroy(rk), "fs_rk4_destroy")
 
 
 def fs_diffusion_advance(state, D, t, u_out, stream=None):

@@ -101,6 +101,9 @@ def test_null_handles_are_rejected(lib):
     assert lib.fs_plan_destroy(None) == 0
     assert lib.fs_state_destroy(None) == 0
     assert lib.fs_state_set_source(None, None, None) == -1
+    assert lib.fs_rk4_step(None, 0.1, 1, None) == -1
+    assert lib.fs_rk4_output(None, None, None, None) == -1
+    assert lib.fs_rk4_destroy(None) == 0
 
 
 def test_binding_raises_with_message(lib):
