@@ -92,8 +92,11 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
 
         def rep():
             fsolve.fs_rk4_step(rk, dt, nst)
-        algo = nst * 10 * spec  # rows write 2 spectra; columns read 5, write 3
+        chunks = -(-nst // 128)
+        # per chunk: U, V read and written once, plus the 1D source tables
+        algo = chunks * 4 * spec + (2 * nst + chunks) * (n // 2 + 1 + n) * 2 * esz
         extra["rk4_steps_per_rep"] = nst
+        extra["modes"] = (n // 2 + 1) * n
         extra["dt"] = dt
         extra["_rk4"] = (rk, plan_rk)
     elif case == "batch_mix":
@@ -162,6 +165,7 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
     if rk4 is not None:
         res["us_per_rk4_step"] = round(1e3 * ms / extra["rk4_steps_per_rep"], 3)
         res["rk4_steps_per_s"] = round(extra["rk4_steps_per_rep"] / (ms / 1e3), 1)
+        res["mode_steps_per_s"] = round(extra["modes"] * extra["rk4_steps_per_rep"] / (ms / 1e3), 1)
     if "solves_per_rep" in extra:
         res["solves_per_s"] = round(extra["solves_per_rep"] / (ms / 1e3), 1)
     if profile:

@@ -3,17 +3,16 @@
 //
 // Per mode the wave equation is the first-order system of
 // Eq. SystemOfODEsForWaveEquation, dU/dt = V, dV/dt = -c^2|w|^2 U + S(t),
-// advanced with the classical fourth-order Runge-Kutta method.  The system is
-// linear, so one step needs the source spectrum at three times only: t (kept
-// from the previous step), t + dt/2 and t + dt.  One step is two launches:
-//   rows    synthesise s(t + dt/2) and s(t + dt) on the grid (no input read)
-//           and run the real row transforms of both      -> wa, wb
-//   columns forward column transforms of wa and wb, then the whole RK4 step
-//           for every mode in registers: read U, V, S(t); write U, V and
-//           S(t + dt) (the next step's S(t)).
-// The source is A exp(-|x - x0(tau)|^2/sigma^2) cos(gamma tau) with the
-// minimum-image distance; the host gives, per stage time, the centre in grid
-// index units and the amplitude A cos(gamma tau).
+// advanced with the classical fourth-order Runge-Kutta method.  The source
+// A exp(-|x - x0(tau)|^2/sigma^2) cos(gamma tau) with the minimum-image
+// distance factorises exactly into exp(-dx^2/sigma^2) exp(-dy^2/sigma^2), so
+// the 2D DFT of its samples is the outer product of two 1D DFTs:
+//   S(a, b, tau) = Gx_tau(a) Gy_tau(b),
+// Gx the half spectrum (a <= nx/2) of A cos(gamma tau) exp(-dx^2/sigma^2)
+// along x, Gy the spectrum of exp(-dy^2/sigma^2) along y.  For a chunk of
+// steps the 1D spectra at every stage time t + j dt/2 are computed first
+// (one CTA per time point and axis, on the same FFT engine as the solves);
+// then every mode runs all steps of the chunk with U and V in registers.
 #pragma once
 #include "fs_units.cuh"
 
@@ -23,165 +22,108 @@ struct RkTime {
   double j0, i0;  // centre in index units: x0 = x_min + j0 hx, y0 = y_min + i0 hy, in [0, n)
   double amp;     // A cos(gamma tau)
 };
-struct RkStep {
-  RkTime mid, end;  // source at t + dt/2 and t + dt
-};
 
-struct RkParams {
-  const RkStep *steps;  // device table
-  int step;             // this launch's entry
-  int init;             // 1: S0 <- forward transform of the source at steps[step].mid
+struct RkSrcParams {
+  const RkTime *times;  // device table of time points
+  int j_first;          // time point of block 0
   double qx, qy;        // (hx/sigma)^2, (hy/sigma)^2: exponent per squared index distance
-  double dt, c2;        // time step, c^2
-  void *U, *V, *S0;     // half spectra [M+1][ny] (x-frequency major), updated in place
-  void *wa, *wb;        // row-transformed source at t + dt/2 and t + dt
+  void *gx, *gy;        // tables [points][M+1] and [points][ny], point 0 = j_first
 };
 
-// Source samples at one stage time.  FP32: the index distance x - j0 is formed
-// as (x - j0_hi) - j0_lo, where the first difference is exact, so the
-// distance keeps its relative accuracy near the centre.
+// x factor at one time point (amplitude folded in).  FP32: the index distance
+// x - j0 is (x - j0_hi) - j0_lo, the first difference exact, so the distance
+// keeps its relative accuracy near the centre.
 template <typename T>
-struct OrbitGen;
+struct OrbitGenX;
 
 template <>
-struct OrbitGen<float> {
-  float j0h, j0l, i0h, i0l, qx, qy, amp, nxf, nyf;
-  __device__ OrbitGen(const RkTime &tm, const RkParams &r, int nx, int ny) {
+struct OrbitGenX<float> {
+  float j0h, j0l, qx, amp, nxf;
+  __device__ OrbitGenX(const RkTime &tm, double q, int nx) {
     split_double(tm.j0, j0h, j0l);
-    split_double(tm.i0, i0h, i0l);
-    qx = (float)r.qx;
-    qy = (float)r.qy;
+    qx = (float)q;
     amp = (float)tm.amp;
     nxf = (float)nx;
-    nyf = (float)ny;
   }
-  __device__ static float wrap(float v, float n) {  // into [-n/2, n/2)
-    return v >= 0.5f * n ? v - n : (v < -0.5f * n ? v + n : v);
+  __device__ float at(int x) const {
+    float d = __fsub_rn(__fsub_rn((float)x, j0h), j0l);
+    d = d >= 0.5f * nxf ? d - nxf : (d < -0.5f * nxf ? d + nxf : d);  // into [-n/2, n/2)
+    return amp * expf(-(d * d) * qx);
   }
-  __device__ cx<float> pair(int y, int x) const {
-    const float dy = wrap(__fsub_rn(__fsub_rn((float)y, i0h), i0l), nyf);
-    const float ey = dy * dy * qy;
-    const float d0 = wrap(__fsub_rn(__fsub_rn((float)x, j0h), j0l), nxf);
-    const float d1 = wrap(__fsub_rn(__fsub_rn((float)(x + 1), j0h), j0l), nxf);
-    return mk<float>(amp * expf(-__fmaf_rn(d0 * d0, qx, ey)), amp * expf(-__fmaf_rn(d1 * d1, qx, ey)));
-  }
+  __device__ cx<float> pair(int, int x) const { return mk<float>(at(x), at(x + 1)); }
 };
 
 template <>
-struct OrbitGen<double> {
-  double j0, i0, qx, qy, amp, nxd, nyd;
-  __device__ OrbitGen(const RkTime &tm, const RkParams &r, int nx, int ny)
-      : j0(tm.j0), i0(tm.i0), qx(r.qx), qy(r.qy), amp(tm.amp), nxd(nx), nyd(ny) {}
-  __device__ static double wrap(double v, double n) {
-    return v >= 0.5 * n ? v - n : (v < -0.5 * n ? v + n : v);
+struct OrbitGenX<double> {
+  double j0, qx, amp, nxd;
+  __device__ OrbitGenX(const RkTime &tm, double q, int nx) : j0(tm.j0), qx(q), amp(tm.amp), nxd(nx) {}
+  __device__ double at(int x) const {
+    double d = (double)x - j0;
+    d = d >= 0.5 * nxd ? d - nxd : (d < -0.5 * nxd ? d + nxd : d);
+    return amp * exp(-(d * d) * qx);
   }
-  __device__ cx<double> pair(int y, int x) const {
-    const double dy = wrap((double)y - i0, nyd);
-    const double ey = dy * dy * qy;
-    const double d0 = wrap((double)x - j0, nxd), d1 = wrap((double)(x + 1) - j0, nxd);
-    return mk<double>(amp * exp(-(d0 * d0 * qx + ey)), amp * exp(-(d1 * d1 * qx + ey)));
-  }
+  __device__ cx<double> pair(int, int x) const { return mk<double>(at(x), at(x + 1)); }
 };
 
-// Row pass: blocks [0, n_row_units) synthesise and transform the source at
-// t + dt/2 into wa; with init == 0, blocks [n_row_units, 2 n_row_units) do
-// t + dt into wb.
+__device__ __forceinline__ float orbit_gy(const RkTime &tm, double q, int ny, int y, float) {
+  float i0h, i0l;
+  split_double(tm.i0, i0h, i0l);
+  const float n = (float)ny;
+  float d = __fsub_rn(__fsub_rn((float)y, i0h), i0l);
+  d = d >= 0.5f * n ? d - n : (d < -0.5f * n ? d + n : d);
+  return expf(-(d * d) * (float)q);
+}
+__device__ __forceinline__ double orbit_gy(const RkTime &tm, double q, int ny, int y, double) {
+  double d = (double)y - tm.i0;
+  d = d >= 0.5 * ny ? d - ny : (d < -0.5 * ny ? d + ny : d);
+  return exp(-(d * d) * q);
+}
+
+// Gx of time point j_first + blockIdx.x: the real transform of one row of
+// length nx (the row unit with a one-row spectrum), written to gx[blockIdx.x].
 template <typename T, int E>
-__device__ __forceinline__ void rk4_rows_body(const Desc &d, const RkParams &r, cx<T> *sm) {
-  int unit = blockIdx.x;
-  const RkStep &st = r.steps[r.step];
-  const bool second = unit >= d.n_row_units;
-  if (second) unit -= d.n_row_units;
-  const OrbitGen<T> g(second ? st.end : st.mid, r, d.nx, d.ny);
-  unit_row_r2c_t<T, E, 0, 0, OrbitGen<T>>(d, unit, d.rows_per_unit, sm, nullptr,
-                                          reinterpret_cast<cx<T> *>(second ? r.wb : r.wa), &g);
+__device__ __forceinline__ void rk4_gx_body(const Desc &d, const RkSrcParams &p, cx<T> *sm) {
+  const int j = blockIdx.x;
+  const OrbitGenX<T> g(p.times[p.j_first + j], p.qx, d.nx);
+  Desc d1 = d;
+  d1.ny = 1;  // spectrum [M+1][1]
+  unit_row_r2c_t<T, E, 0, 0, OrbitGenX<T>>(d1, 0, 1, sm, nullptr,
+                                           reinterpret_cast<cx<T> *>(p.gx) + (size_t)j * (d.M + 1), &g);
 }
 
-__device__ __forceinline__ float rk_w2(const Desc &d, int a, int b, float c2) {
-  const float2 wx = reinterpret_cast<const float2 *>(d.wx2)[a];
-  const float2 wy = reinterpret_cast<const float2 *>(d.wy2)[b];
-  return c2 * __fadd_rn(__fadd_rn(wx.x, wy.x), __fadd_rn(wx.y, wy.y));
-}
-__device__ __forceinline__ double rk_w2(const Desc &d, int a, int b, double c2) {
-  return c2 * (reinterpret_cast<const double *>(d.wx2)[a] + reinterpret_cast<const double *>(d.wy2)[b]);
-}
-
-// Column pass: thread (rho, t) of column a = blockIdx.x * cols_per_unit + rho
-// holds the frequencies b = t + Tseg*s after the forward transforms.
+// Gy of time point j_first + blockIdx.x: the complex transform of length ny of
+// exp(-dy^2/sigma^2), written to gy[blockIdx.x] in natural order.
 template <typename T, int E>
-__device__ __forceinline__ void rk4_cols_body(const Desc &d, const RkParams &r, cx<T> *sm) {
-  const int L = d.ny, M = d.M, Tseg = L / E, cnt = d.cols_per_unit;
-  const int tid = threadIdx.x;
-  const int rho = tid / Tseg, t = tid - rho * Tseg;
-  const int a = blockIdx.x * cnt + rho;
-  const bool active = (rho < cnt) && (a <= M);
-  const XLayout lay{rho * L, 1};
-  const cx<T> *tw = reinterpret_cast<const cx<T> *>(d.tw_y);
-  const size_t cofs = (size_t)(active ? a : 0) * L;
-  cx<T> *S0 = reinterpret_cast<cx<T> *>(r.S0) + cofs;
-  cx<T> p[E];
+__device__ __forceinline__ void rk4_gy_body(const Desc &d, const RkSrcParams &p, cx<T> *sm) {
+  const int j = blockIdx.x, L = d.ny, Tseg = L / E;
+  const int t = threadIdx.x;
+  const bool active = t < Tseg;
+  const RkTime tm = p.times[p.j_first + j];
+  cx<T> u[E];
+#pragma unroll
+  for (int s = 0; s < E; ++s) u[s] = active ? mk<T>(orbit_gy(tm, p.qy, L, t + Tseg * s, T(0)), T(0)) : zero_cx<T>();
+  fft_any<T, E, 0, 1, 1>(u, sm, XLayout{0, 1}, active, t, Tseg, L, d.rp_col, reinterpret_cast<const cx<T> *>(d.tw_y));
   if (active) {
-    const cx<T> *src = reinterpret_cast<const cx<T> *>(r.wa) + cofs;
+    cx<T> *dst = reinterpret_cast<cx<T> *>(p.gy) + (size_t)j * L;
 #pragma unroll
-    for (int s = 0; s < E; ++s) p[s] = ldg_cg(src + t + Tseg * s);
-  } else {
-#pragma unroll
-    for (int s = 0; s < E; ++s) p[s] = zero_cx<T>();
-  }
-  fft_any<T, E, 0, 1, 1>(p, sm, lay, active, t, Tseg, L, d.rp_col, tw);
-  if (r.init) {  // uniform over the launch
-    if (active) {
-#pragma unroll
-      for (int s = 0; s < E; ++s) S0[t + Tseg * s] = p[s];
-    }
-    return;
-  }
-  cx<T> q[E];
-  if (active) {
-    const cx<T> *src = reinterpret_cast<const cx<T> *>(r.wb) + cofs;
-#pragma unroll
-    for (int s = 0; s < E; ++s) q[s] = ldg_cg(src + t + Tseg * s);
-  } else {
-#pragma unroll
-    for (int s = 0; s < E; ++s) q[s] = zero_cx<T>();
-  }
-  __syncthreads();
-  fft_any<T, E, 0, 1, 1>(q, sm, lay, active, t, Tseg, L, d.rp_col, tw);
-  if (!active) return;
-  cx<T> *U = reinterpret_cast<cx<T> *>(r.U) + cofs;
-  cx<T> *V = reinterpret_cast<cx<T> *>(r.V) + cofs;
-  const T h = (T)r.dt, hh = (T)(0.5 * r.dt), h6 = (T)(r.dt / 6.0), c2 = (T)r.c2;
-#pragma unroll
-  for (int s = 0; s < E; ++s) {
-    const int b = t + Tseg * s;
-    const T w2 = rk_w2(d, a, b, c2);
-    const cx<T> u = ldg_cg(U + b), v = ldg_cg(V + b), s0 = ldg_cg(S0 + b);
-    const cx<T> smid = p[s], s1 = q[s];
-    // slopes of (U, V): k = (V, S - w2 U)
-    const cx<T> k1u = v, k1v = s0 - w2 * u;
-    const cx<T> k2u = v + hh * k1v, k2v = smid - w2 * (u + hh * k1u);
-    const cx<T> k3u = v + hh * k2v, k3v = smid - w2 * (u + hh * k2u);
-    const cx<T> k4u = v + h * k3v, k4v = s1 - w2 * (u + h * k3u);
-    U[b] = u + h6 * (k1u + T(2) * (k2u + k3u) + k4u);
-    V[b] = v + h6 * (k1v + T(2) * (k2v + k3v) + k4v);
-    S0[b] = s1;
+    for (int s = 0; s < E; ++s) dst[t + Tseg * s] = u[s];
   }
 }
 
-typedef void (*Rk4Kernel)(const Desc, const RkParams);
+typedef void (*Rk4Kernel)(const Desc, const RkSrcParams);
 
-#define FS_RK4_DECL(T, E)                                                  \
-  __global__ void k_rk4r_##T##_##E(const Desc d, const RkParams r);        \
-  __global__ void k_rk4c_##T##_##E(const Desc d, const RkParams r);
+#define FS_RK4_DECL(T, E)                                                    \
+  __global__ void k_rk4gx_##T##_##E(const Desc d, const RkSrcParams p);      \
+  __global__ void k_rk4gy_##T##_##E(const Desc d, const RkSrcParams p);
 
-#define FS_RK4_DEF(T, E)                                                                    \
-  __global__ void __launch_bounds__(512) k_rk4r_##T##_##E(const Desc d, const RkParams r) { \
-    extern __shared__ __align__(16) unsigned char fs_smem[];                                \
-    rk4_rows_body<T, E>(d, r, reinterpret_cast<cx<T> *>(fs_smem));                          \
-  }                                                                                         \
-  __global__ void __launch_bounds__(512) k_rk4c_##T##_##E(const Desc d, const RkParams r) { \
-    extern __shared__ __align__(16) unsigned char fs_smem[];                                \
-    rk4_cols_body<T, E>(d, r, reinterpret_cast<cx<T> *>(fs_smem));                          \
+#define FS_RK4_DEF(T, E)                                                                        \
+  __global__ void __launch_bounds__(512) k_rk4gx_##T##_##E(const Desc d, const RkSrcParams p) { \
+    extern __shared__ __align__(16) unsigned char fs_smem[];                                    \
+    rk4_gx_body<T, E>(d, p, reinterpret_cast<cx<T> *>(fs_smem));                                \
+  }                                                                                             \
+  __global__ void __launch_bounds__(512) k_rk4gy_##T##_##E(const Desc d, const RkSrcParams p) { \
+    extern __shared__ __align__(16) unsigned char fs_smem[];                                    \
+    rk4_gy_body<T, E>(d, p, reinterpret_cast<cx<T> *>(fs_smem));                                \
   }
 
 FS_FOR_EACH_E_float(FS_RK4_DECL)
@@ -189,15 +131,15 @@ FS_FOR_EACH_E_double(FS_RK4_DECL)
 
 #define FS_RK4_CASE(T, E) \
   case E:                 \
-    return rows ? k_rk4r_##T##_##E : k_rk4c_##T##_##E;
+    return x_axis ? k_rk4gx_##T##_##E : k_rk4gy_##T##_##E;
 template <typename T>
-inline Rk4Kernel rk4_kernel(int e, bool rows);
+inline Rk4Kernel rk4_kernel(int e, bool x_axis);
 template <>
-inline Rk4Kernel rk4_kernel<float>(int e, bool rows) {
+inline Rk4Kernel rk4_kernel<float>(int e, bool x_axis) {
   switch (e) { FS_FOR_EACH_E_float(FS_RK4_CASE) default: return nullptr; }
 }
 template <>
-inline Rk4Kernel rk4_kernel<double>(int e, bool rows) {
+inline Rk4Kernel rk4_kernel<double>(int e, bool x_axis) {
   switch (e) { FS_FOR_EACH_E_double(FS_RK4_CASE) default: return nullptr; }
 }
 
