@@ -32,6 +32,9 @@ Pinning status (what fixes each function independently of itself):
                            finite differences and a spectral Laplacian from
                            numpy.fft, initial conditions, zero-mode
                            polynomials                               -> pinned
+  solve.*_complex          complex fields: a complex plane wave's closed
+                           form per operator, and linearity against the
+                           (pinned) real solves on re and im parts   -> pinned
   rk4.wave_rk4_spectrum    RK4 of Eq. SystemOfODEsForWaveEquation: the
                            closed-form one-step propagator, 4th-order
                            convergence to the constant-source closed form,
@@ -52,6 +55,9 @@ from .solve import (  # noqa: F401
     state_spectrum,
     diffusion_source_spectrum,
     wave_source_spectrum,
+    poisson_complex,
+    diffusion_complex,
+    wave_complex,
 )
 from .rk4 import wave_rk4_spectrum  # noqa: F401
 from . import closed_forms  # noqa: F401

@@ -34,6 +34,9 @@ import numpy as np
 from .dft import dft2, idft2
 
 __all__ = [
+    "poisson_complex",
+    "diffusion_complex",
+    "wave_complex",
     "diffusion_source_spectrum",
     "wave_source_spectrum",
     "omega_axis",
@@ -156,6 +159,27 @@ def wave(u0, v0, c, t, lx, ly, sign=-1, want_v=False):
         return u
     v = _real_part(idft2(V, sign=-sign), "wave v")
     return u, v
+
+
+# ---------------------------------------------------------------- complex fields
+# Sec. II.B lets the samples p_jk be complex; the solves are the same
+# spectral operators on the full spectrum, returned as complex fields.
+def poisson_complex(f, lx, ly, sign=-1):
+    """Zero-mean solution of lap u = f - mean(f) for a complex field f."""
+    F = dft2(np.asarray(f, dtype=np.complex128), sign=sign)
+    return idft2(poisson_spectrum(F, lx, ly), sign=-sign)
+
+
+def diffusion_complex(u0, D, t, lx, ly, sign=-1):
+    F = dft2(np.asarray(u0, dtype=np.complex128), sign=sign)
+    return idft2(diffusion_spectrum(F, D, t, lx, ly), sign=-sign)
+
+
+def wave_complex(u0, v0, c, t, lx, ly, sign=-1):
+    F = dft2(np.asarray(u0, dtype=np.complex128), sign=sign)
+    G = None if v0 is None else dft2(np.asarray(v0, dtype=np.complex128), sign=sign)
+    U, _ = wave_spectrum(F, G, c, t, lx, ly)
+    return idft2(U, sign=-sign)
 
 
 # ---------------------------------------------------------------- constant sources

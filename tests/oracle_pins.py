@@ -320,6 +320,35 @@ def pin_wave_source_pde(n=32, c=0.9, t=0.21, dt=2e-4, seed=14):
     return max(e1, e2, rel(a, f), rel(b, g))
 
 
+# ------------------------------------------------------------ complex fields
+def pin_complex_plane_wave(nx=24, ny=20, lx=1.7, ly=0.8, kx=3, ky=-5, D=0.001, c=1.1, t=0.4):
+    """exp(i (wx x + wy y)) is an eigenfunction: Poisson -> -mode/|w|^2,
+    diffusion -> mode exp(-D|w|^2 t), wave (v0 = 0) -> mode cos(c|w|t); the
+    negative ky checks that a complex field uses the full spectrum."""
+    x = (lx / nx) * np.arange(nx)
+    y = (ly / ny) * np.arange(ny)
+    wx, wy = 2 * np.pi * kx / lx, 2 * np.pi * ky / ly
+    mode = np.exp(1j * (wy * y[:, None] + wx * x[None, :]))
+    w2 = wx * wx + wy * wy
+    e1 = rel(oracle.poisson_complex(mode, lx, ly), -mode / w2)
+    e2 = rel(oracle.diffusion_complex(mode, D, t, lx, ly), mode * math.exp(-D * w2 * t))
+    e3 = rel(oracle.wave_complex(mode, None, c, t, lx, ly), mode * math.cos(c * math.sqrt(w2) * t))
+    return max(e1, e2, e3)
+
+
+def pin_complex_linearity(n=32, seed=17):
+    """The operators are real multipliers: solve(a + i b) = solve(a) + i solve(b)
+    with the real solves (pinned above) on a and b."""
+    rng = np.random.default_rng(seed)
+    a, b, g = rng.standard_normal((n, n)), rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    e1 = rel(oracle.poisson_complex(a + 1j * b, 1.0, 1.3), oracle.poisson(a, 1.0, 1.3) + 1j * oracle.poisson(b, 1.0, 1.3))
+    e2 = rel(oracle.diffusion_complex(a + 1j * b, 0.02, 0.3, 1.0, 1.3),
+             oracle.diffusion(a, 0.02, 0.3, 1.0, 1.3) + 1j * oracle.diffusion(b, 0.02, 0.3, 1.0, 1.3))
+    e3 = rel(oracle.wave_complex(a + 1j * b, g + 0j, 0.9, 0.37, 1.0, 1.3),
+             oracle.wave(a, g, 0.9, 0.37, 1.0, 1.3) + 1j * oracle.wave(b, None, 0.9, 0.37, 1.0, 1.3))
+    return max(e1, e2, e3)
+
+
 # ----------------------------------------------------------------------- RK4
 def pin_rk4_propagator(nx=8, ny=6, lx=1.3, ly=0.9, c=1.1, dt=0.06, seed=15):
     """One RK4 step of the free oscillator is the degree-4 Taylor polynomial of
@@ -409,6 +438,8 @@ PINS = {
     "sign_independence": (pin_sign_independence, 1e-13),
     "diffusion_source_pde": (pin_diffusion_source_pde, 1e-6),
     "wave_source_pde": (pin_wave_source_pde, 1e-5),
+    "complex_plane_wave": (pin_complex_plane_wave, 1e-13),
+    "complex_linearity": (pin_complex_linearity, 1e-13),
     "rk4_propagator": (pin_rk4_propagator, 1e-13),
     "rk4_constant_source_order": (pin_rk4_constant_source_order, 0.15),
     "rk4_orbit_self_convergence": (pin_rk4_orbit_self_convergence, 0.1),

@@ -133,6 +133,20 @@ def _rk4_variant(weights=(1, 2, 2, 1), src_stage=("start", "mid", "mid", "end"),
     return fn
 
 
+def _poisson_complex_real_only(f, lx, ly, sign=-1):
+    # drops the imaginary part of the input (a real-only solve)
+    F = odft.dft2(np.real(np.asarray(f)).astype(np.complex128), sign=sign)
+    return odft.idft2(osolve.poisson_spectrum(F, lx, ly), sign=-sign)
+
+
+def _diffusion_complex_half_spectrum(u0, D, t, lx, ly, sign=-1):
+    # treats negative x frequencies as positive-index frequencies (no shift)
+    F = odft.dft2(np.asarray(u0, dtype=np.complex128), sign=sign)
+    ny, nx = F.shape
+    w2 = (2 * np.pi * np.arange(nx) / lx)[None, :] ** 2 + osolve.omega_axis(ny, ly)[:, None] ** 2
+    return odft.idft2(F * np.exp(-D * t * w2), sign=-sign)
+
+
 _ORIG_DFT1 = odft.dft1
 _ORIG_WAVE = osolve.wave_spectrum
 
@@ -150,6 +164,8 @@ MUTANTS = {
     "dft1_sign_ignored": [(odft, "dft1", _dft1_sign_ignored), (oracle, "dft1", _dft1_sign_ignored)],
     "diffusion_source_gain_sign": [(oracle, "diffusion_source_spectrum", _diffusion_source_gain_sign)],
     "wave_source_printed_form": [(oracle, "wave_source_spectrum", _wave_source_printed)],
+    "complex_real_only": [(oracle, "poisson_complex", _poisson_complex_real_only)],
+    "complex_no_shift": [(oracle, "diffusion_complex", _diffusion_complex_half_spectrum)],
     "rk4_weights": [(oracle, "wave_rk4_spectrum", _rk4_variant(weights=(1, 1, 2, 2)))],
     "rk4_source_at_step_start": [(oracle, "wave_rk4_spectrum",
                                   _rk4_variant(src_stage=("start", "start", "start", "start")))],
