@@ -99,6 +99,21 @@ fs_status fs_diffusion_solve(fs_plan plan, const void *u0, double D, double t, v
 fs_status fs_wave_solve(fs_plan plan, const void *u0, const void *v0, double c, double t,
                         void *u, fs_stream stream);
 
+/* ---------------------------------------------------------------- complex fields
+ * The same three solves for complex fields (Sec. II.B: the samples p_jk may
+ * be complex; the full spectrum is used, a = 0..nx-1).  Fields are
+ * interleaved complex (re, im) of the plan dtype, [ny][nx], device memory
+ * owned by the caller; outputs may alias inputs.  Operators, parameters and
+ * errors as for the real solves (Poisson removes the complex mean).  The
+ * first complex call allocates a full-spectrum workspace (nx ny complex; a
+ * second one for the wave with v0) kept until fs_plan_destroy.  FS_ERR_SIZE
+ * for FP64 plans with nx = 5 * 2^k, k >= 8 (no length-nx radix plan). */
+fs_status fs_poisson_solve_c(fs_plan plan, const void *f, void *u, fs_stream stream);
+fs_status fs_diffusion_solve_c(fs_plan plan, const void *u0, double D, double t, void *u,
+                               fs_stream stream);
+fs_status fs_wave_solve_c(fs_plan plan, const void *u0, const void *v0, double c, double t,
+                          void *u, fs_stream stream);
+
 /* ---------------------------------------------------------------- kept states
  * fs_state_create: forward-transform the initial data once and keep the
  * half-spectra U0 (and V0 when v0 != NULL) on the device (Sec. III.B/III.C:

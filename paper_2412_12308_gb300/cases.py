@@ -51,6 +51,14 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
         def rep():
             fsolve.fs_poisson_solve(plan, fd, out)
         algo = 3 * (real + spec)  # three passes: R2C, column, C2R
+    elif case == "poisson_c":
+        # complex field, full spectrum: rows C2C, columns, inverse rows C2C
+        fc = torch.complex(fd, torch.flip(fd, (0,))).contiguous()
+        outc = torch.empty_like(fc)
+
+        def rep():
+            fsolve.fs_poisson_solve_c(plan, fc, outc)
+        algo = 3 * 2 * n * n * 2 * esz
     elif case == "wave_solve":
         def rep():
             fsolve.fs_wave_solve(plan, fd, None, 1.0, 0.37, out)

@@ -195,8 +195,9 @@ Desc base_desc(const fs_plan_s *p) {
   return d;
 }
 
+// x part for all nx frequencies (complex fields use a <= nx-1; real fields a <= nx/2)
 size_t fac_bytes(const fs_plan_s *p) {
-  return (size_t)(p->M + 1 + p->ny) * (p->dtype == FS_F64 ? sizeof(double) : sizeof(float2));
+  return (size_t)(p->nx + p->ny) * (p->dtype == FS_F64 ? sizeof(double) : sizeof(float2));
 }
 
 // Signed-index angular wavenumber squared: (2 pi a'/L)^2, a' = a (a <= n/2) else a - n.
@@ -266,6 +267,15 @@ fs_status fs_plan_create(int nx, int ny, double lx, double ly, int dtype, fs_pla
     return set_error(FS_ERR_SIZE, "fs_plan_create: no radix plan for this size");
   tmp.csize = dtype == FS_F64 ? 2 * sizeof(double) : 2 * sizeof(float);
   tmp.tc = make_tiles(nx, ny, tmp.rp_row, tmp.rp_col, tmp.csize);
+  // complex (C2C) rows of length nx; some FP64 lengths (5 * 2^k, k >= 8) need
+  // more radix-2 stages than a plan holds: complex solves then report FS_ERR_SIZE
+  if (!make_rp(nx, dtype == FS_F64, &tmp.rp_rowc)) memset(&tmp.rp_rowc, 0, sizeof tmp.rp_rowc);
+  if (tmp.rp_rowc.e) {  // complex row tiles: up to 16 rows, <= 512 threads, ~96 KB exchange
+    const int tr = nx / tmp.rp_rowc.e;
+    int cr = 16;
+    while (cr > 1 && (cr * tr > kMaxThreads || tmp.csize * padded_len(cr * nx) > 96 * 1024)) cr >>= 1;
+    tmp.tc.rows_per_unit_c = cr > ny ? ny : cr;
+  }
   const int small_max = env_int("FS_SMALL_MAX", 128 * 128);
   tmp.standalone_small = (nx * ny <= small_max) && tmp.tc.small_smem2 > 0;
   tmp.spec_bytes = (size_t)(tmp.M + 1) * ny * tmp.csize;
@@ -282,8 +292,8 @@ fs_status fs_plan_create(int nx, int ny, double lx, double ly, int dtype, fs_pla
   // ---- host tables in FP64
   const bool f64 = dtype == FS_F64;
   const int M = tmp.M;
-  std::vector<double> wx2d(M + 1), wy2d(ny);
-  for (int a = 0; a <= M; ++a) wx2d[a] = omega2_axis(a, nx, lx);
+  std::vector<double> wx2d(nx), wy2d(ny);  // x: all nx frequencies (complex fields)
+  for (int a = 0; a < nx; ++a) wx2d[a] = omega2_axis(a, nx, lx);
   for (int b = 0; b < ny; ++b) wy2d[b] = omega2_axis(b, ny, ly);
   auto twiddles = [&](int n, std::vector<unsigned char> &buf) {
     buf.resize((size_t)n * tmp.csize);
@@ -362,6 +372,8 @@ fs_status fs_plan_destroy(fs_plan p) {
   cudaFree(p->tables);
   cudaFree(p->work_u);
   cudaFree(p->work_v);
+  cudaFree(p->work_c);
+  cudaFree(p->work_cv);
   cudaFree(p->fac);
   delete p;
   return FS_OK;
@@ -404,6 +416,60 @@ static cudaError_t run_desc(const fs_plan_s *p, const Desc &d, cudaStream_t s) {
 static fs_status run(const fs_plan_s *p, const Desc &d, fs_stream stream, const char *what) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = p->dtype == FS_F64 ? run_desc<double>(p, d, s) : run_desc<float>(p, d, s);
+  if (e != cudaSuccess) return cuda_error(e, what);
+  return FS_OK;
+}
+
+// ---------------------------------------------------------------- complex fields
+// The full x spectrum: descriptor with M = nx - 1 (columns a = 0..nx-1 of the
+// x-frequency-major spectrum; the column units, operators and factor tables
+// cover them unchanged), complex row tiles and the length-nx radix plan.
+static Desc complex_desc(const fs_plan_s *p) {
+  Desc d = base_desc(p);
+  d.M = p->nx - 1;
+  d.rp_row = p->rp_rowc;
+  d.rows_per_unit = p->tc.rows_per_unit_c;
+  d.n_row_units = (p->ny + d.rows_per_unit - 1) / d.rows_per_unit;
+  d.n_col_units = (p->nx + d.cols_per_unit - 1) / d.cols_per_unit;
+  d.n_fac_units = (p->nx + p->ny + kFactorPerUnit - 1) / kFactorPerUnit;
+  d.work_u = p->work_c;
+  d.work_v = p->work_cv;
+  d.small = 0;
+  return d;
+}
+
+static fs_status ensure_work_c(fs_plan p, bool two) {
+  const size_t bytes = (size_t)p->nx * p->ny * p->csize;
+  cudaError_t e = cudaSuccess;
+  if (!p->work_c) e = alloc_dev(&p->work_c, bytes);
+  if (e == cudaSuccess && two && !p->work_cv) e = alloc_dev(&p->work_cv, bytes);
+  if (e != cudaSuccess) return cuda_error(e, "complex workspace allocation");
+  return FS_OK;
+}
+
+template <typename T>
+static cudaError_t run_complex_desc(const Desc &d, cudaStream_t s) {
+  typedef Launch<T> L;
+  const PassKernels pk = pass_kernels<T>(d.rp_row.e);
+  const int threads = round_up32(d.rows_per_unit * (d.nx / d.rp_row.e));
+  const size_t smem = sizeof(cx<T>) * (size_t)padded_len(d.rows_per_unit * d.nx);
+  const int fields = (d.op == OP_WAVE && (d.flags & F_HAS_V0)) ? 2 : 1;
+  cudaError_t e = cudaSuccess;
+  if (d.op == OP_DIFFUSION) e = L::factor(d, s);
+  if (e == cudaSuccess) e = L::launch(pk.c2cf, d.n_row_units * fields, threads, smem, d, s, PC_R2C);
+  if (e == cudaSuccess) e = L::cols(d, s);
+  if (e == cudaSuccess) e = L::launch(pk.c2ci, d.n_row_units, threads, smem, d, s, PC_C2R);
+  return e;
+}
+
+static fs_status run_complex(fs_plan p, Desc &d, fs_stream stream, const char *what) {
+  if (!p->rp_rowc.e) return set_error(FS_ERR_SIZE, std::string(what) + ": no complex row plan for this nx and dtype");
+  fs_status st = ensure_work_c(p, (d.flags & F_HAS_V0) != 0);
+  if (st != FS_OK) return st;
+  d.work_u = p->work_c;
+  d.work_v = p->work_cv;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = p->dtype == FS_F64 ? run_complex_desc<double>(d, s) : run_complex_desc<float>(d, s);
   if (e != cudaSuccess) return cuda_error(e, what);
   return FS_OK;
 }
@@ -469,6 +535,45 @@ fs_status fs_wave_solve(fs_plan p, const void *u0, const void *v0, double c, dou
   d.p_c = c;
   d.p_t = t;
   return run(p, d, stream, "fs_wave_solve");
+}
+
+fs_status fs_poisson_solve_c(fs_plan p, const void *f, void *u, fs_stream stream) {
+  if (!p || !f || !u) return set_error(FS_ERR_ARG, "fs_poisson_solve_c: NULL argument");
+  Desc d = complex_desc(p);
+  d.op = OP_POISSON;
+  d.in_u = f;
+  d.out_u = u;
+  return run_complex(p, d, stream, "fs_poisson_solve_c");
+}
+
+fs_status fs_diffusion_solve_c(fs_plan p, const void *u0, double D, double t, void *u, fs_stream stream) {
+  if (!p || !u0 || !u) return set_error(FS_ERR_ARG, "fs_diffusion_solve_c: NULL argument");
+  if (!(D >= 0.0) || !(t >= 0.0) || !std::isfinite(D * t))
+    return set_error(FS_ERR_ARG, "fs_diffusion_solve_c: need finite D >= 0 and t >= 0");
+  Desc d = complex_desc(p);
+  d.op = OP_DIFFUSION;
+  d.in_u = u0;
+  d.out_u = u;
+  d.p_dt = D * t;
+  d.p_d = D;
+  d.p_t = t;
+  return run_complex(p, d, stream, "fs_diffusion_solve_c");
+}
+
+fs_status fs_wave_solve_c(fs_plan p, const void *u0, const void *v0, double c, double t, void *u,
+                          fs_stream stream) {
+  if (!p || !u0 || !u) return set_error(FS_ERR_ARG, "fs_wave_solve_c: NULL argument");
+  if (!(c > 0.0) || !std::isfinite(c) || !std::isfinite(t))
+    return set_error(FS_ERR_ARG, "fs_wave_solve_c: need finite c > 0 and finite t");
+  Desc d = complex_desc(p);
+  d.op = OP_WAVE;
+  d.flags = v0 ? F_HAS_V0 : 0;
+  d.in_u = u0;
+  d.in_v = v0;
+  d.out_u = u;
+  d.p_c = c;
+  d.p_t = t;
+  return run_complex(p, d, stream, "fs_wave_solve_c");
 }
 
 fs_status fs_state_create(fs_plan p, const void *u0, const void *v0, fs_stream stream,

@@ -23,6 +23,7 @@ bool size_supported(int n);
 
 struct TileConfig {
   int rows_per_unit;  // row passes
+  int rows_per_unit_c;  // complex (C2C) row passes, length nx
   int cols_per_unit;  // column pass
   int small_rows, small_cols;
   size_t small_smem1, small_smem2;  // small-path smem with one / two resident spectra (0: too big)
@@ -35,6 +36,7 @@ struct fs_plan_s {
   double lx, ly;
   int device;
   fs::RadixPlan rp_row, rp_col;
+  fs::RadixPlan rp_rowc;  // length nx: complex (C2C) row transforms
   fs::TileConfig tc;
   bool standalone_small;  // single-kernel path for one-off calls
   size_t csize;           // bytes per complex element
@@ -44,6 +46,7 @@ struct fs_plan_s {
   double *wx2d, *wy2d;
   // device workspace
   void *work_u, *work_v, *fac;
+  void *work_c, *work_cv;  // full spectra nx*ny for complex fields (allocated on first use)
   size_t spec_bytes;  // (M+1)*ny complex
 };
 

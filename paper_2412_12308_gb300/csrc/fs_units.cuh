@@ -112,6 +112,51 @@ __device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt_
   __syncthreads();
 }
 
+// ------------------------------------------------------------ row C2C (complex fields)
+// Complex fields use the full x spectrum: rows y0..y0+cnt-1 of a complex field
+// [ny][nx] <-> spec[a][y], a = 0..nx-1 (x-frequency major, like the half
+// spectrum of real fields).  Same thread mapping as the real row units; the
+// length-nx plan is d.rp_row of the complex descriptor.  The inverse runs by
+// conjugation (conj of the forward DFT of conj); no scaling (1/(nx ny) is in
+// the spectral multiplier).
+template <typename T, int E>
+__device__ __forceinline__ void unit_row_c2c_t(const Desc &d, int unit, int cnt, cx<T> *sm, const cx<T> *in,
+                                               cx<T> *spec, cx<T> *out, bool inverse) {
+  const int N = d.nx, ny = d.ny, Tseg = N / E;
+  const int tid = threadIdx.x;
+  const int t = tid / cnt, rho = tid - t * cnt;
+  const int y = unit * cnt + rho;
+  const bool active = (t < Tseg) && (y < ny);
+  const XLayout lay{rho, cnt};
+  const cx<T> *tw = reinterpret_cast<const cx<T> *>(d.tw_x);
+  cx<T> v[E];
+  if (active) {
+    if (inverse) {
+#pragma unroll
+      for (int s = 0; s < E; ++s) v[s] = conj(ldg_cg(spec + (size_t)(t + Tseg * s) * ny + y));
+    } else {
+      const cx<T> *row = in + (size_t)y * N;
+#pragma unroll
+      for (int s = 0; s < E; ++s) v[s] = ldg_cg(row + t + Tseg * s);
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();
+  }
+  fft_any<T, E, 0, 0, 1>(v, sm, lay, active, t, Tseg, N, d.rp_row, tw);
+  if (active) {
+    if (inverse) {
+      cx<T> *row = out + (size_t)y * N;
+#pragma unroll
+      for (int s = 0; s < E; ++s) row[t + Tseg * s] = conj(v[s]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < E; ++s) spec[(size_t)(t + Tseg * s) * ny + y] = v[s];
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------ row C2R
 // spec[a][y] (a = 0..M) for rows y0..y0+cnt-1 -> real rows.  With
 // F_a = X_a + conj X_{M-a} and G_a = (X_a - conj X_{M-a}) e^{+2 pi i a/nx},
@@ -416,7 +461,9 @@ __device__ __forceinline__ void kbody_c2r(const Desc &d, cx<T> *sm) {
   __global__ void k_c2r_##T##_##E(const Desc d);                           \
   __global__ void k_col1_##T##_##E(const Desc d);                          \
   __global__ void k_col2_##T##_##E(const Desc d);                          \
-  __global__ void k_cols_##T##_##E(const Desc d);
+  __global__ void k_cols_##T##_##E(const Desc d);                          \
+  __global__ void k_c2cf_##T##_##E(const Desc d);                          \
+  __global__ void k_c2ci_##T##_##E(const Desc d);
 
 #define FS_UNIT_DECL(T, E)                                                                     \
   FS_KERNEL_DECL(T, E)                                                                         \
@@ -474,6 +521,22 @@ __device__ __forceinline__ void kbody_c2r(const Desc &d, cx<T> *sm) {
                            reinterpret_cast<cx<T> *>(d.work_u),                                 \
                            reinterpret_cast<cx<T> *>(d.work_v), false);                         \
   }                                                                                             \
+  __global__ void __launch_bounds__(512) k_c2cf_##T##_##E(const Desc d) {                       \
+    extern __shared__ __align__(16) unsigned char fs_smem[];                                    \
+    int unit = blockIdx.x;                                                                      \
+    const bool second = unit >= d.n_row_units;                                                  \
+    if (second) unit -= d.n_row_units;                                                          \
+    unit_row_c2c_t<T, E>(d, unit, d.rows_per_unit, reinterpret_cast<cx<T> *>(fs_smem),          \
+                         reinterpret_cast<const cx<T> *>(second ? d.in_v : d.in_u),             \
+                         reinterpret_cast<cx<T> *>(second ? d.work_v : d.work_u), nullptr,      \
+                         false);                                                                \
+  }                                                                                             \
+  __global__ void __launch_bounds__(512) k_c2ci_##T##_##E(const Desc d) {                       \
+    extern __shared__ __align__(16) unsigned char fs_smem[];                                    \
+    unit_row_c2c_t<T, E>(d, blockIdx.x, d.rows_per_unit, reinterpret_cast<cx<T> *>(fs_smem),    \
+                         nullptr, reinterpret_cast<cx<T> *>(d.work_u),                          \
+                         reinterpret_cast<cx<T> *>(d.out_u), true);                             \
+  }                                                                                             \
   __global__ void __launch_bounds__(512) k_cols_##T##_##E(const Desc d) {                       \
     extern __shared__ __align__(16) unsigned char fs_smem[];                                    \
     unit_col_t<T, E, true, 0, 0, true>(d, blockIdx.x, d.cols_per_unit,                          \
@@ -525,12 +588,12 @@ FS_FOR_EACH_E_double(FS_UNIT_DECL)
 
 // Host-side kernel lookup by register tile.
 struct PassKernels {
-  PassKernel r2c, c2r, col1, col2, cols;
+  PassKernel r2c, c2r, col1, col2, cols, c2cf, c2ci;
 };
 #define FS_PK_CASE(T, E)                                                                      \
   case E:                                                                                     \
     return PassKernels{k_r2c_##T##_##E, k_c2r_##T##_##E, k_col1_##T##_##E, k_col2_##T##_##E, \
-                       k_cols_##T##_##E};
+                       k_cols_##T##_##E, k_c2cf_##T##_##E, k_c2ci_##T##_##E};
 template <typename T>
 inline PassKernels pass_kernels(int e);
 template <>

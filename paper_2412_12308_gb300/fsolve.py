@@ -61,6 +61,9 @@ _SIGS = {
                                                _vp, _vp, _vp]),
     "fs_diffusion_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "fs_poisson_solve_c": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "fs_diffusion_solve_c": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "fs_wave_solve_c": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_state_create": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "fs_state_destroy": (ctypes.c_int, [_vp]),
     "fs_state_reset": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -198,6 +201,24 @@ def fs_wave_solve(plan, u0, v0, c, t, u, stream=None):
     load()
     _check(_lib.fs_wave_solve(plan, _ptr(u0), _ptr(v0), float(c), float(t), _ptr(u), _stream(stream)),
            "fs_wave_solve")
+
+
+def fs_poisson_solve_c(plan, f, u, stream=None):
+    """Complex fields: f, u are complex64/complex128 tensors [ny][nx]."""
+    load()
+    _check(_lib.fs_poisson_solve_c(plan, _ptr(f), _ptr(u), _stream(stream)), "fs_poisson_solve_c")
+
+
+def fs_diffusion_solve_c(plan, u0, D, t, u, stream=None):
+    load()
+    _check(_lib.fs_diffusion_solve_c(plan, _ptr(u0), float(D), float(t), _ptr(u), _stream(stream)),
+           "fs_diffusion_solve_c")
+
+
+def fs_wave_solve_c(plan, u0, v0, c, t, u, stream=None):
+    load()
+    _check(_lib.fs_wave_solve_c(plan, _ptr(u0), _ptr(v0), float(c), float(t), _ptr(u), _stream(stream)),
+           "fs_wave_solve_c")
 
 
 def fs_state_create(plan, u0, v0=None, stream=None):
