@@ -218,8 +218,8 @@ def run_ours(args, dist):
     state = fsolve.fs_state_create(plan, u0d)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     ts = [float(t) for t in times]
-    reqs = [fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, state=state, out_u=out[j], D=D, t=t)
-            for j, t in enumerate(ts)]
+    reqs = fsolve.fs_request_array([fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, state=state, out_u=out[j],
+                                                      D=D, t=t) for j, t in enumerate(ts)])
 
     def step(src):
         # one forward transform into the kept spectrum, then all 100 advances

@@ -33,6 +33,7 @@ namespace {
 
 constexpr size_t kChunkBytes = 24u << 20;     // intermediate bytes per pipeline chunk
 constexpr size_t kMaxDynSmem = 227u * 1024u;  // per-CTA dynamic shared memory limit
+constexpr int kMaxSlots = 3;                   // in-flight batches per device (serving keeps 3)
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -387,19 +388,34 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: cudaGetDevice");
-  // an idle slot of this device (its last batch finished), else a new one
-  Slot *s = nullptr;
+  // an idle slot of this device (its last batch finished); else a new one, up
+  // to kMaxSlots per device; else wait for the oldest pending batch (a new
+  // slot means device allocations and a graph capture on the host while the
+  // GPU may be idle)
+  Slot *s = nullptr, *oldest = nullptr;
+  int on_dev = 0;
   for (Slot *c : g_slots) {
     if (c->device != dev) continue;
+    ++on_dev;
     if (c->pending) {
       const cudaError_t q = cudaEventQuery(c->ev);
-      if (q == cudaErrorNotReady) continue;
+      if (q == cudaErrorNotReady) {
+        if (!oldest || c->ticket < oldest->ticket) oldest = c;
+        continue;
+      }
       if (q != cudaSuccess) return cuda_error(q, "fs_batch_submit: event query");
       c->pending = false;
       remember(c->ticket, c->h_status[1]);
     }
     s = c;
     break;
+  }
+  if (!s && oldest && on_dev >= kMaxSlots) {
+    e = cudaEventSynchronize(oldest->ev);
+    if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: wait for a slot");
+    oldest->pending = false;
+    remember(oldest->ticket, oldest->h_status[1]);
+    s = oldest;
   }
   if (!s) {
     s = new Slot();

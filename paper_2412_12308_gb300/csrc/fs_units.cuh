@@ -72,18 +72,33 @@ __device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt_
   const XLayout lay{rho, cnt};
   const cx<T> *tw = reinterpret_cast<const cx<T> *>(d.tw_x);
   cx<T> v[E];
-  if (active) {
-    if constexpr (std::is_void<GEN>::value) {
-      const cx<T> *row = reinterpret_cast<const cx<T> *>(in + (size_t)y * d.nx);
+  if constexpr (std::is_void<GEN>::value) {
+    // the tile's rows are contiguous runs of M pairs: load them with all the
+    // CTA's threads along the rows (coalesced), stage them in the exchange
+    // buffer ([m][row], the layout of the exchange below), then take the slots
+    const int y0 = unit * cnt, rows = min(cnt, ny - y0), nthr = blockDim.x;
+    const cx<T> *tile = reinterpret_cast<const cx<T> *>(in + (size_t)y0 * d.nx);
+    for (int idx = tid; idx < rows * M; idx += nthr) {
+      const int r = idx / M, m = idx - r * M;
+      sm[padi(r + m * cnt)] = ldg_cg(tile + (size_t)r * M + m);
+    }
+    __syncthreads();
+    if (active) {
 #pragma unroll
-      for (int s = 0; s < E; ++s) v[s] = ldg_cg(row + t + Tseg * s);
+      for (int s = 0; s < E; ++s) v[s] = sm[padi(rho + (t + Tseg * s) * cnt)];
     } else {
 #pragma unroll
-      for (int s = 0; s < E; ++s) v[s] = gen->pair(y, 2 * (t + Tseg * s));
+      for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();
     }
+    __syncthreads();
   } else {
+    if (active) {
 #pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();
+      for (int s = 0; s < E; ++s) v[s] = gen->pair(y, 2 * (t + Tseg * s));
+    } else {
+#pragma unroll
+      for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();
+    }
   }
   fft_any<T, E, MC, CC, 2>(v, sm, lay, active, t, Tseg, M, d.rp_row, tw);
   __syncthreads();
@@ -209,10 +224,21 @@ __device__ __forceinline__ void unit_row_c2r_t(const Desc &d, int unit, int cnt_
   }
   fft_any<T, E, MC, CC, 2>(v, sm, lay, active, t, Tseg, M, d.rp_row, tw);
   conj_tile(v);
+  // stage the tile in the exchange buffer ([m][row]) and store whole rows with
+  // all the CTA's threads along the rows (coalesced)
+  __syncthreads();
   if (active) {
-    cx<T> *row = reinterpret_cast<cx<T> *>(out + (size_t)y * d.nx);
 #pragma unroll
-    for (int s = 0; s < E; ++s) row[t + Tseg * s] = v[s];
+    for (int s = 0; s < E; ++s) sm[padi(rho + (t + Tseg * s) * cnt)] = v[s];
+  }
+  __syncthreads();
+  {
+    const int y0 = unit * cnt, rows = min(cnt, ny - y0), nthr = blockDim.x;
+    cx<T> *tile = reinterpret_cast<cx<T> *>(out + (size_t)y0 * d.nx);
+    for (int idx = tid; idx < rows * M; idx += nthr) {
+      const int r = idx / M, m = idx - r * M;
+      tile[(size_t)r * M + m] = sm[padi(r + m * cnt)];
+    }
   }
   __syncthreads();
 }

@@ -310,10 +310,15 @@ def fs_request(op, plan=None, state=None, in_u=None, in_v=None, out_u=None, out_
                      int(keep), int(parent))
 
 
+def fs_request_array(reqs):
+    """Marshal a list of FsRequest once into a C array (reusable across submits)."""
+    return (FsRequest * len(reqs))(*reqs)
+
+
 def fs_batch_submit(reqs, stream=None):
-    """Submit a list of FsRequest; returns the batch ticket."""
+    """Submit a list of FsRequest (or an array from fs_request_array); returns the ticket."""
     load()
-    arr = (FsRequest * len(reqs))(*reqs)
+    arr = reqs if isinstance(reqs, ctypes.Array) else (FsRequest * len(reqs))(*reqs)
     ticket = ctypes.c_uint64()
     _check(_lib.fs_batch_submit(arr, len(reqs), ctypes.byref(ticket), _stream(stream)), "fs_batch_submit")
     return ticket.value
