@@ -61,6 +61,7 @@ struct Slot {
   int key_descs = -1, key_units = -1, key_grid = -1, key_dtype = -1;
   size_t key_smem = 0;
   unsigned long long key_wait = 0;
+  int key_threads = 0;
 };
 
 std::mutex g_mu;
@@ -128,17 +129,6 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
     d.work_u = d.work_v = nullptr;
     d.fac = nullptr;
     d.out_u = r.out_u;
-    // column groups that fill a 512-thread batch CTA (the count does not
-    // change a column's arithmetic)
-    {
-      const int tseg = p->ny / p->rp_col.e;
-      int cc = kMaxThreads / tseg;
-      if (cc > 32) cc = 32;
-      if (cc < 1) cc = 1;
-      while (cc > 1 && (size_t)padded_len(cc * p->ny) * p->csize > 100 * 1024) cc >>= 1;
-      d.cols_per_unit = cc;
-      d.n_col_units = (p->M + 1 + cc - 1) / cc;
-    }
     switch (r.op) {
       case FS_OP_POISSON:
         if (!r.in_u) return set_error(FS_ERR_ARG, "fs_batch_submit: Poisson without input");
@@ -230,6 +220,53 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
   }
   bp->ws_off.resize(n);
   for (int k = 0; k < n; ++k) bp->ws_off[k] = ws_off[items[k].idx];
+
+  // CTA size: 256 threads (two CTAs per SM) when every problem run as units
+  // has row and column transforms of at most 256 threads and none is a
+  // single-CTA small problem (its whole solve would run on half the threads),
+  // else 512.  Measured on GB300: 100 advances of 1024^2 +9 %, a 512-problem
+  // mix with small problems -18 % at 256.  Tile shapes follow; a row's or
+  // column's arithmetic does not depend on how many share a CTA.
+  {
+    int need = 1;
+    for (int k = 0; k < n; ++k) {
+      if (bp->direct[k]) continue;
+      const Desc &d = bp->descs[k];
+      need = std::max(need, std::max(d.M / d.rp_row.e, d.ny / d.rp_col.e));
+      if (d.small) need = kMaxThreads;
+    }
+    const int bt = need <= 256 ? 256 : kMaxThreads;
+    if (const char *v = getenv("FS_BATCH_THREADS")) {
+      int maxe = 1;  // the override may force 256 when every transform fits
+      for (int k = 0; k < n; ++k)
+        if (!bp->direct[k])
+          maxe = std::max(maxe, std::max(bp->descs[k].M / bp->descs[k].rp_row.e, bp->descs[k].ny / bp->descs[k].rp_col.e));
+      if (atoi(v) == 512 || (atoi(v) == 256 && maxe <= 256)) bp->threads = atoi(v);
+      else bp->threads = bt;
+    } else {
+      bp->threads = bt;
+    }
+    for (int k = 0; k < n; ++k) {
+      if (bp->direct[k]) continue;
+      Desc &d = bp->descs[k];
+      const int tseg = d.ny / d.rp_col.e, tr = d.M / d.rp_row.e;
+      const size_t cs = bp->dtype == FS_F64 ? 16 : 8;
+      int cc = bp->threads / tseg;
+      if (cc > 32) cc = 32;
+      if (cc < 1) cc = 1;
+      while (cc > 1 && (size_t)padded_len(cc * d.ny) * cs > 100 * 1024) cc >>= 1;
+      d.cols_per_unit = cc;
+      int rr = d.rows_per_unit;  // the plan's row tile
+      if (rr * tr > bp->threads) rr = std::max(1, bp->threads / tr);
+      d.rows_per_unit = rr;
+      d.n_row_units = (d.ny + rr - 1) / rr;
+      d.n_col_units = (d.M + 1 + cc - 1) / cc;
+      if (d.small) {
+        if (d.small_rows * tr > bp->threads) d.small_rows = std::max(1, bp->threads / tr);
+        if (d.small_cols * tseg > bp->threads) d.small_cols = std::max(1, bp->threads / tseg);
+      }
+    }
+  }
 
   // Work-unit granularity: each unit covers G row tiles / column groups, G
   // chosen so the batch still has several units per SM (grouping does not
@@ -484,7 +521,18 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
   memcpy(s->h_units, bp.units.data(), nu * sizeof(int4));
 
   int per_sm = 0, sms = 0;
-  e = dtype == FS_F64 ? Launch<double>::batch_occupancy(smem, &per_sm) : Launch<float>::batch_occupancy(smem, &per_sm);
+  int threads = bp.threads;
+  auto occupancy = [&](int th) {
+    return dtype == FS_F64 ? Launch<double>::batch_occupancy(th, smem, &per_sm)
+                           : Launch<float>::batch_occupancy(th, smem, &per_sm);
+  };
+  e = occupancy(threads);
+  // 256-thread CTAs only pay when two fit on an SM (a resident small problem's
+  // half spectrum can take most of the shared memory); the tiles also fit 512
+  if (e == cudaSuccess && threads == 256 && per_sm < 2) {
+    threads = kMaxThreads;
+    e = occupancy(threads);
+  }
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: occupancy");
   if (per_sm < 1) return set_error(FS_ERR_SIZE, "fs_batch_submit: batch kernel does not fit on an SM");
@@ -492,7 +540,8 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
   if ((size_t)grid > nu) grid = (int)nu;
 
   const bool same = s->gexec && s->key_descs == (int)nd && s->key_units == (int)nu && s->key_grid == grid &&
-                    s->key_dtype == dtype && s->key_smem == smem && s->key_wait == wait_ns;
+                    s->key_dtype == dtype && s->key_smem == smem && s->key_wait == wait_ns &&
+                    s->key_threads == threads;
   if (!same) {
     drop_graph(s);
     cudaGraph_t g = nullptr;
@@ -504,9 +553,9 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
       cudaMemsetAsync(s->d_done, 0, 5 * nd * sizeof(int), s->cap);
       cudaError_t le = dtype == FS_F64
                            ? Launch<double>::batch(s->d_descs, s->d_units, (int)nu, s->d_ctl, s->d_done,
-                                                   grid, smem, wait_ns, s->cap)
+                                                   grid, threads, smem, wait_ns, s->cap)
                            : Launch<float>::batch(s->d_descs, s->d_units, (int)nu, s->d_ctl, s->d_done,
-                                                  grid, smem, wait_ns, s->cap);
+                                                  grid, threads, smem, wait_ns, s->cap);
       cudaMemcpyAsync(s->h_status, s->d_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->cap);
       e = cudaStreamEndCapture(s->cap, &g);
       if (e == cudaSuccess && le != cudaSuccess) e = le;
@@ -523,6 +572,7 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
     s->key_dtype = dtype;
     s->key_smem = smem;
     s->key_wait = wait_ns;
+    s->key_threads = threads;
   } else {
     g_launches.fetch_add(1, std::memory_order_relaxed);  // the replayed k_batch
   }

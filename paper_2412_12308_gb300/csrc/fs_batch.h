@@ -17,6 +17,7 @@ struct BatchPlan {
   size_t arena_bytes = 0;
   size_t smem = 0;
   int dtype = -1;
+  int threads = 512;             // batch CTA size: 256 when every unit fits (two CTAs per SM)
 };
 
 // Validate requests and build descriptors + work table (no device work).

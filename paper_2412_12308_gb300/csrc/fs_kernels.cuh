@@ -69,8 +69,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_batch(const Desc *__restrict__ descs,
+// THREADS = 512 (one CTA per SM at 128 registers) or 256 (two CTAs per SM:
+// one unit's barrier waits overlap the other's work); the batch plan picks 256
+// when every problem's transforms fit and shapes its tiles accordingly.
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1) k_batch(const Desc *__restrict__ descs,
                                                        const int4 *__restrict__ units, int n_units,
                                                        int *ctl, int *done,
                                                        unsigned long long wait_ns) {
@@ -310,18 +313,24 @@ struct Launch {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
   }
+  typedef void (*BatchKernel)(const Desc *, const int4 *, int, int *, int *, unsigned long long);
+  static BatchKernel batch_kernel(int threads) {
+    return threads == 256 ? k_batch<T, 256> : k_batch<T, kMaxThreads>;
+  }
   static cudaError_t batch(const Desc *descs, const int4 *units, int n_units, int *ctl, int *done,
-                           int grid, size_t smem, unsigned long long wait_ns, cudaStream_t s) {
-    cudaError_t e = set_smem((const void *)k_batch<T>, smem);
+                           int grid, int threads, size_t smem, unsigned long long wait_ns, cudaStream_t s) {
+    BatchKernel k = batch_kernel(threads);
+    cudaError_t e = set_smem((const void *)k, smem);
     if (e != cudaSuccess) return e;
-    k_batch<T><<<grid, kMaxThreads, smem, s>>>(descs, units, n_units, ctl, done, wait_ns);
+    k<<<grid, threads, smem, s>>>(descs, units, n_units, ctl, done, wait_ns);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
   }
-  static cudaError_t batch_occupancy(size_t smem, int *per_sm) {
-    cudaError_t e = set_smem((const void *)k_batch<T>, smem);
+  static cudaError_t batch_occupancy(int threads, size_t smem, int *per_sm) {
+    BatchKernel k = batch_kernel(threads);
+    cudaError_t e = set_smem((const void *)k, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<T>, kMaxThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);
   }
 };
 

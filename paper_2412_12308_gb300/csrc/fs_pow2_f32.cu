@@ -165,15 +165,18 @@ __global__ void __launch_bounds__(ColT<L>::THREADS, min_blocks<ColT<L>::THREADS>
 #define FS_P2_COLS(X) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
 
 // ---------------------------------------------------------------- device dispatch for batch / small paths
-template <int M>
+// row tiles of the standalone kernels (CC = p2_row_cnt(M)) and of 256-thread
+// batch CTAs (CC = 256 / (M/16) where that is smaller)
+template <int M, int CC = RowK<M>::CC>
 __device__ __noinline__ void p2_r2c_unit(const Desc &d, int unit, cx<float> *sm, const float *in, cx<float> *spec) {
-  unit_row_r2c_t<float, 16, M, RowK<M>::CC>(d, unit, RowK<M>::CC, sm, in, spec);
+  unit_row_r2c_t<float, 16, M, CC>(d, unit, CC, sm, in, spec);
 }
-template <int M>
+template <int M, int CC = RowK<M>::CC>
 __device__ __noinline__ void p2_c2r_unit(const Desc &d, int unit, cx<float> *sm, const cx<float> *spec, float *out,
                                          bool sh) {
-  unit_row_c2r_t<float, 16, M, RowK<M>::CC>(d, unit, RowK<M>::CC, sm, spec, out, sh);
+  unit_row_c2r_t<float, 16, M, CC>(d, unit, CC, sm, spec, out, sh);
 }
+constexpr int p2_row_cnt_256(int M) { return (M / 16) * p2_row_cnt(M) <= 256 ? p2_row_cnt(M) : 256 / (M / 16); }
 template <int L>
 __device__ __noinline__ void p2_col1_unit(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu,
                                           cx<float> *wv, bool sh) {
@@ -181,12 +184,19 @@ __device__ __noinline__ void p2_col1_unit(const Desc &d, int unit, int cnt, cx<f
 }
 
 __device__ bool p2_unit_r2c(const Desc &d, int unit, int cnt, cx<float> *sm, const float *in, cx<float> *spec) {
-  if (d.rp_row.e != 16 || cnt != p2_row_cnt(d.M)) return false;
+  if (d.rp_row.e != 16) return false;
   switch (d.M) {
-#define C(m)                                 \
-  case m:                                    \
-    p2_r2c_unit<m>(d, unit, sm, in, spec);   \
-    return true;
+#define C(m)                                                                   \
+  case m:                                                                      \
+    if (cnt == p2_row_cnt(m)) {                                                \
+      p2_r2c_unit<m>(d, unit, sm, in, spec);                                   \
+      return true;                                                             \
+    }                                                                          \
+    if (p2_row_cnt_256(m) != p2_row_cnt(m) && cnt == p2_row_cnt_256(m)) {      \
+      p2_r2c_unit<m, p2_row_cnt_256(m)>(d, unit, sm, in, spec);                \
+      return true;                                                             \
+    }                                                                          \
+    return false;
     FS_P2_ROWS(C)
 #undef C
     default:
@@ -195,12 +205,19 @@ __device__ bool p2_unit_r2c(const Desc &d, int unit, int cnt, cx<float> *sm, con
 }
 __device__ bool p2_unit_c2r(const Desc &d, int unit, int cnt, cx<float> *sm, const cx<float> *spec, float *out,
                             bool sh) {
-  if (d.rp_row.e != 16 || cnt != p2_row_cnt(d.M)) return false;
+  if (d.rp_row.e != 16) return false;
   switch (d.M) {
-#define C(m)                                        \
-  case m:                                           \
-    p2_c2r_unit<m>(d, unit, sm, spec, out, sh);     \
-    return true;
+#define C(m)                                                                   \
+  case m:                                                                      \
+    if (cnt == p2_row_cnt(m)) {                                                \
+      p2_c2r_unit<m>(d, unit, sm, spec, out, sh);                              \
+      return true;                                                             \
+    }                                                                          \
+    if (p2_row_cnt_256(m) != p2_row_cnt(m) && cnt == p2_row_cnt_256(m)) {      \
+      p2_c2r_unit<m, p2_row_cnt_256(m)>(d, unit, sm, spec, out, sh);           \
+      return true;                                                             \
+    }                                                                          \
+    return false;
     FS_P2_ROWS(C)
 #undef C
     default:
