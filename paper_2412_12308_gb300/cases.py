@@ -63,6 +63,21 @@ def run(case, n, iters, warmup, dtype=0, profile=True):
         def rep():
             fsolve.fs_wave_solve(plan, fd, None, 1.0, 0.37, out)
         algo = 3 * (real + spec)
+    elif case == "wave_solve_v0":
+        # initial velocity: two row transforms, two-field column pass
+        gd = torch.flip(fd, (1,)).contiguous()
+
+        def rep():
+            fsolve.fs_wave_solve(plan, fd, gd, 1.0, 0.37, out)
+        algo = 2 * (real + spec) + 3 * spec + spec + real
+    elif case == "wave_adv_v":
+        # advance with the velocity output: two inverse column transforms, two C2R fields
+        state = fsolve.fs_state_create(plan, fd)
+        vout = torch.empty_like(out)
+
+        def rep():
+            fsolve.fs_wave_advance(state, 1.0, 0.37, out, vout)
+        algo = spec + 2 * spec + 2 * (spec + real)
     elif case == "wave_adv":
         state = fsolve.fs_state_create(plan, fd)
 

@@ -53,8 +53,11 @@ __global__ void __launch_bounds__(RowK<M>::THREADS, min_blocks<RowK<M>::THREADS>
                                            out, false);
 }
 
+// two register tiles (TWO): at most 128 registers per thread (two 256-thread
+// CTAs or one 512-thread CTA per SM) so that both tiles stay in registers
 template <int L, bool TWO>
-__global__ void __launch_bounds__(ColK<L>::THREADS, min_blocks<ColK<L>::THREADS>()) k_col_p2(const Desc d) {
+__global__ void __launch_bounds__(ColK<L>::THREADS, TWO ? (ColK<L>::THREADS >= 512 ? 1 : 2)
+                                                        : min_blocks<ColK<L>::THREADS>()) k_col_p2(const Desc d) {
   extern __shared__ __align__(16) unsigned char fs_smem[];
   unit_col_t<float, 16, TWO, L, ColK<L>::CC>(d, blockIdx.x, ColK<L>::CC, reinterpret_cast<cx<float> *>(fs_smem),
                                              reinterpret_cast<cx<float> *>(d.work_u),

@@ -16,7 +16,8 @@ struct ColS {
 };
 
 template <int L, bool TWO>
-__global__ void __launch_bounds__(ColS<L>::THREADS, ColS<L>::MINB) k_col_p2s(const Desc d) {
+__global__ void __launch_bounds__(ColS<L>::THREADS, TWO ? (ColS<L>::THREADS >= 512 ? 1 : 2) : ColS<L>::MINB)
+    k_col_p2s(const Desc d) {
   extern __shared__ __align__(16) unsigned char fs_smem[];
   unit_col_t<float, 16, TWO, L, ColS<L>::CC, true>(d, blockIdx.x, ColS<L>::CC,
                                                    reinterpret_cast<cx<float> *>(fs_smem),
