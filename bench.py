@@ -311,23 +311,32 @@ def run_ours(args, dist):
                 "algorithmic_bytes_per_launch": algo,
                 "per_kernel_ms": {k: round(v[1] / max(1, v[0]), 5) for k, v in prof.items() if v[0]}}
 
-    # ---- end to end through the C ABI with host buffers (pinned)
+    # ---- end to end through the C ABI with host buffers (pinned): u0 is copied
+    # to the device, and the batch's C2R units store the 100 outputs straight
+    # into the pinned host array (mapped into the GPU's address space; on GB300
+    # the stores cross NVLink-C2C while the batch computes, instead of a copy
+    # after it)
     h_u0 = torch.from_numpy(u0).pin_memory()
     h_out = torch.empty((len(ts), N, N), dtype=torch.float32).pin_memory()
+    reqs_host = fsolve.fs_request_array([fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, state=state,
+                                                           out_u=h_out[j].data_ptr(), D=D, t=t)
+                                         for j, t in enumerate(ts)])
     e2e_ms = []
-    for k in range(max(3, args.steps // 2)):
+    for k in range(max(3, args.steps // 2) + 2):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         u0d.copy_(h_u0, non_blocking=True)
-        step(u0d)
-        h_out.copy_(out, non_blocking=True)
+        fsolve.fs_state_reset(state, u0d)
+        fsolve.fs_batch_submit(reqs_host)
         b.record()
         torch.cuda.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
+        if k >= 2:  # the first two build the host-output batch's graphs
+            e2e_ms.append(a.elapsed_time(b))
     e2e_step = dist.max(statistics.median(e2e_ms))
     e2e = {"value": dist.world * len(ts) / (e2e_step / 1e3), "unit": "solves/s",
-           "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(len(ts) * N * N * 4)}
+           "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(len(ts) * N * N * 4),
+           "d2h": "outputs stored by the kernels into pinned host memory"}
 
     # ---- comparators on the same GPU: this library one call per solve, and the
     # plain torch.fft path (rfft2 -> FP32 multiply -> irfft2, separate launches)

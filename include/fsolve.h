@@ -210,7 +210,11 @@ fs_status fs_rk4_destroy(fs_rk4 rk);
  * (and `in_v` for FS_OP_WAVE, may be NULL) and write `out_u`; the advance ops
  * read `state` and write `out_u` (and `out_v` for FS_OP_WAVE_ADVANCE, may be
  * NULL).  `plan` gives the grid; every plan in a batch must have the same
- * dtype.  Pointers are device pointers owned by the caller.
+ * dtype.  Pointers are owned by the caller and must be accessible from the
+ * device: device memory, or host memory mapped into the device's address
+ * space (pinned memory under unified addressing); output fields in host
+ * memory are stored by the kernels directly (on GB300 over NVLink-C2C,
+ * overlapped with the batch's compute).
  */
 enum {
   FS_OP_POISSON = 0,

@@ -167,6 +167,44 @@ def test_batched_advances_from_kept_states(gpu_lib, dtype):
         fsolve.fs_plan_destroy(plan)
 
 
+def test_outputs_in_pinned_host_memory(gpu_lib):
+    """Output fields in pinned host memory (mapped into the device's address
+    space) are stored by the kernels directly: identical to device outputs,
+    for the batch (small and three-pass problems) and a per-call advance."""
+    n1, n2 = 128, 1024
+    rng = np.random.default_rng(44)
+    plans, states, reqs_d, reqs_h, dev, hst = [], [], [], [], [], []
+    try:
+        for n in (n1, n2):
+            plan = fsolve.fs_plan_create(n, n, 1.0, 1.0, F32)
+            plans.append(plan)
+            u0 = torch.tensor(rng.standard_normal((n, n)), dtype=torch.float32, device="cuda")
+            st = fsolve.fs_state_create(plan, u0)
+            states.append(st)
+            for t in (0.001, 0.01):
+                od = torch.empty((n, n), dtype=torch.float32, device="cuda")
+                oh = torch.full((n, n), float("nan"), dtype=torch.float32).pin_memory()
+                dev.append(od)
+                hst.append(oh)
+                reqs_d.append(fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, state=st, out_u=od, D=0.1, t=t))
+                reqs_h.append(fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, state=st, out_u=oh.data_ptr(),
+                                                D=0.1, t=t))
+        fsolve.fs_batch_wait(fsolve.fs_batch_submit(reqs_d), 30_000_000)
+        fsolve.fs_batch_wait(fsolve.fs_batch_submit(reqs_h), 30_000_000)
+        torch.cuda.synchronize()
+        for od, oh in zip(dev, hst):
+            assert torch.equal(od.cpu(), oh)
+        oh = torch.empty((n2, n2), dtype=torch.float32).pin_memory()
+        fsolve.fs_diffusion_advance(states[1], 0.1, 0.01, oh.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(dev[3].cpu(), oh)
+    finally:
+        for st in states:
+            fsolve.fs_state_destroy(st)
+        for plan in plans:
+            fsolve.fs_plan_destroy(plan)
+
+
 def test_bounded_wait_expires_without_fault(gpu_lib, monkeypatch):
     probs = wl.batch_mix(seed=5, count=6, sizes=(512, 1024))
     P = Problems(probs)
