@@ -145,6 +145,21 @@ fs_status fs_state_reset(fs_state state, const void *u0, const void *v0, fs_stre
  * fs_state_reset. */
 fs_status fs_state_set_source(fs_state state, const void *s, fs_stream stream);
 
+/* Checkpoints of a kept state (the state is just its spectra: Sec. III.B/III.C
+ * fix the solution at any t from f-hat, g-hat and s-hat).
+ * fs_state_bytes: size of a checkpoint (a header plus U0, V0 when present and
+ *   the source spectrum when attached).
+ * fs_state_save: write the checkpoint into host memory dst (cap >= that size);
+ *   synchronises the stream.  FS_ERR_ARG if dst is NULL or too small.
+ * fs_state_load: restore a checkpoint into a state of a plan with the same
+ *   grid, domain and dtype and the same v0 presence (FS_ERR_ARG otherwise, the
+ *   state unchanged); attaches the saved source (allocating its buffer if
+ *   needed) or detaches it.  Synchronises the stream.  Advances of the loaded
+ *   state equal those of the saved one (absolute-time closed forms). */
+fs_status fs_state_bytes(fs_state state, size_t *bytes);
+fs_status fs_state_save(fs_state state, void *dst, size_t cap, fs_stream stream);
+fs_status fs_state_load(fs_state state, const void *src, size_t bytes, fs_stream stream);
+
 /* fs_diffusion_advance: u(t) from a kept state, t absolute (>= 0) from the
  * state's initial data: inverse 2D DFT of U0 exp(-D|omega|^2 t)
  * (Eq. solCalorFourier), plus the source term when one is attached

@@ -662,6 +662,87 @@ fs_status fs_state_destroy(fs_state s) {
   return FS_OK;
 }
 
+// ---------------------------------------------------------------- checkpoints
+// Header + the kept spectra (U0, then V0 when present, then the source
+// spectrum when attached), each (nx/2+1) * ny complex of the plan dtype.
+struct StateHeader {
+  char magic[8];  // "FSSTATE1"
+  int32_t nx, ny, dtype, has_v, has_s, pad;
+  double lx, ly;
+};
+
+fs_status fs_state_bytes(fs_state s, size_t *bytes) {
+  if (!s || !bytes) return set_error(FS_ERR_ARG, "fs_state_bytes: NULL argument");
+  *bytes = sizeof(StateHeader) + s->plan->spec_bytes * (1 + (s->has_v ? 1 : 0) + (s->has_s ? 1 : 0));
+  return FS_OK;
+}
+
+fs_status fs_state_save(fs_state s, void *dst, size_t cap, fs_stream stream) {
+  size_t need = 0;
+  fs_status st = fs_state_bytes(s, &need);
+  if (st != FS_OK) return st;
+  if (!dst || cap < need) return set_error(FS_ERR_ARG, "fs_state_save: destination missing or too small");
+  const fs_plan_s *p = s->plan;
+  StateHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, "FSSTATE1", 8);
+  h.nx = p->nx;
+  h.ny = p->ny;
+  h.dtype = p->dtype;
+  h.has_v = s->has_v ? 1 : 0;
+  h.has_s = s->has_s ? 1 : 0;
+  h.lx = p->lx;
+  h.ly = p->ly;
+  memcpy(dst, &h, sizeof h);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  char *q = static_cast<char *>(dst) + sizeof h;
+  const void *parts[3] = {s->su, s->has_v ? s->sv : nullptr, s->has_s ? s->ss : nullptr};
+  cudaError_t e = cudaSuccess;
+  for (const void *src : parts) {
+    if (!src || e != cudaSuccess) continue;
+    e = cudaMemcpyAsync(q, src, p->spec_bytes, cudaMemcpyDeviceToHost, cs);
+    q += p->spec_bytes;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_error(e, "fs_state_save");
+  return FS_OK;
+}
+
+fs_status fs_state_load(fs_state s, const void *src, size_t bytes, fs_stream stream) {
+  if (!s || !src) return set_error(FS_ERR_ARG, "fs_state_load: NULL argument");
+  if (bytes < sizeof(StateHeader)) return set_error(FS_ERR_ARG, "fs_state_load: checkpoint too short");
+  StateHeader h;
+  memcpy(&h, src, sizeof h);
+  const fs_plan_s *p = s->plan;
+  if (memcmp(h.magic, "FSSTATE1", 8) != 0) return set_error(FS_ERR_ARG, "fs_state_load: not a state checkpoint");
+  if (h.nx != p->nx || h.ny != p->ny || h.dtype != p->dtype || h.lx != p->lx || h.ly != p->ly)
+    return set_error(FS_ERR_ARG, "fs_state_load: checkpoint is for another grid, domain or dtype");
+  if ((h.has_v != 0) != s->has_v)
+    return set_error(FS_ERR_ARG, "fs_state_load: v0 presence must match the state");
+  const size_t need = sizeof h + p->spec_bytes * (1 + (h.has_v ? 1 : 0) + (h.has_s ? 1 : 0));
+  if (bytes < need) return set_error(FS_ERR_ARG, "fs_state_load: checkpoint truncated");
+  if (h.has_s && !s->ss) {
+    cudaError_t e = alloc_dev(&s->ss, p->spec_bytes);
+    if (e != cudaSuccess) {
+      s->ss = nullptr;
+      return cuda_error(e, "fs_state_load: device allocation");
+    }
+  }
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const char *q = static_cast<const char *>(src) + sizeof h;
+  void *parts[3] = {s->su, h.has_v ? s->sv : nullptr, h.has_s ? s->ss : nullptr};
+  cudaError_t e = cudaSuccess;
+  for (void *dst : parts) {
+    if (!dst || e != cudaSuccess) continue;
+    e = cudaMemcpyAsync(dst, q, p->spec_bytes, cudaMemcpyHostToDevice, cs);
+    q += p->spec_bytes;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);  // the caller may reuse `src` on return
+  if (e != cudaSuccess) return cuda_error(e, "fs_state_load");
+  s->has_s = h.has_s != 0;
+  return FS_OK;
+}
+
 fs_status fs_diffusion_advance(fs_state s, double D, double t, void *u_out, fs_stream stream) {
   if (!s || !u_out) return set_error(FS_ERR_ARG, "fs_diffusion_advance: NULL argument");
   if (!(D >= 0.0) || !(t >= 0.0) || !std::isfinite(D * t))

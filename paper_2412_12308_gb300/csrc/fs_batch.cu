@@ -576,10 +576,10 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
   } else {
     g_launches.fetch_add(1, std::memory_order_relaxed);  // the replayed k_batch
   }
-  void *tok = nullptr;
-  if (prof_on()) prof_begin(PC_BATCH, stream, &tok);
-  e = cudaGraphLaunch(s->gexec, stream);
-  if (tok) prof_end(tok, stream);
+  {
+    ProfScope ps(PC_BATCH, stream);
+    e = cudaGraphLaunch(s->gexec, stream);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(s->ev, stream);
   if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: graph launch");
   s->pending = true;

@@ -19,14 +19,24 @@ enum ProfClass { PC_R2C = 0, PC_COL = 1, PC_C2R = 2, PC_FACTOR = 3, PC_SMALL = 4
 bool prof_on();
 void prof_begin(int cls, cudaStream_t s, void **tok);
 void prof_end(void *tok, cudaStream_t s);
+// NVTX ranges around each pass launch (env FS_NVTX=1; no-ops without a tool)
+bool nvtx_on();
+void nvtx_push(int cls);
+void nvtx_pop();
 struct ProfScope {
   void *tok = nullptr;
   cudaStream_t s;
+  bool nv = false;
   ProfScope(int cls, cudaStream_t st) : s(st) {
     if (prof_on()) prof_begin(cls, st, &tok);
+    if (nvtx_on()) {
+      nvtx_push(cls);
+      nv = true;
+    }
   }
   ~ProfScope() {
     if (tok) prof_end(tok, s);
+    if (nv) nvtx_pop();
   }
 };
 

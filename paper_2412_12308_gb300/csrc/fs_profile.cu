@@ -1,4 +1,9 @@
-// fs_profile.cu -- optional per-launch CUDA-event timing of the library's kernels.
+// fs_profile.cu -- optional per-launch CUDA-event timing of the library's
+// kernels, and optional NVTX ranges per pass (env FS_NVTX=1) for timeline
+// tools; the NVTX v3 calls are no-ops unless a tool is attached.
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -18,6 +23,19 @@ std::atomic<bool> g_on{false};
 }  // namespace
 
 bool prof_on() { return g_on.load(std::memory_order_relaxed); }
+
+bool nvtx_on() {
+  static const bool on = [] {
+    const char *v = getenv("FS_NVTX");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+void nvtx_push(int cls) {
+  static const char *names[PC_N] = {"fs row R2C", "fs column", "fs row C2R", "fs factor", "fs small", "fs batch"};
+  nvtxRangePushA(cls >= 0 && cls < PC_N ? names[cls] : "fs");
+}
+void nvtx_pop() { nvtxRangePop(); }
 
 void prof_begin(int cls, cudaStream_t s, void **tok) {
   Rec *r = new Rec{cls, nullptr, nullptr};

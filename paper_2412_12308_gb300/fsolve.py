@@ -68,6 +68,9 @@ _SIGS = {
     "fs_state_destroy": (ctypes.c_int, [_vp]),
     "fs_state_reset": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "fs_state_set_source": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fs_state_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "fs_state_save": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "fs_state_load": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     "fs_diffusion_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_advance": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp]),
     "fs_rk4_create": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.POINTER(FsOrbitSource), _vp, _vp,
@@ -285,6 +288,23 @@ def fs_rk4_time(rk):
 def fs_rk4_destroy(rk):
     load()
     _check(_lib.fs_rk4_destroy(rk), "fs_rk4_destroy")
+
+
+def fs_state_save(state, stream=None):
+    """Checkpoint of a kept state as bytes (host memory)."""
+    load()
+    n = ctypes.c_size_t()
+    _check(_lib.fs_state_bytes(state, ctypes.byref(n)), "fs_state_bytes")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(_lib.fs_state_save(state, buf, n.value, _stream(stream)), "fs_state_save")
+    return buf.raw
+
+
+def fs_state_load(state, data, stream=None):
+    """Restore a checkpoint (bytes from fs_state_save) into a compatible state."""
+    load()
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(_lib.fs_state_load(state, buf, len(data), _stream(stream)), "fs_state_load")
 
 
 def fs_diffusion_advance(state, D, t, u_out, stream=None):

@@ -105,6 +105,8 @@ def test_null_handles_are_rejected(lib):
     assert lib.fs_rk4_output(None, None, None, None) == -1
     assert lib.fs_rk4_destroy(None) == 0
     assert lib.fs_poisson_solve_c(None, None, None, None) == -1
+    assert lib.fs_state_load(None, None, 0, None) == -1
+    assert lib.fs_state_save(None, None, 0, None) == -1
 
 
 def test_binding_raises_with_message(lib):
