@@ -53,11 +53,13 @@ __global__ void __launch_bounds__(RowK<M>::THREADS, min_blocks<RowK<M>::THREADS>
                                            out, false);
 }
 
-// two register tiles (TWO): at most 128 registers per thread (two 256-thread
-// CTAs or one 512-thread CTA per SM) so that both tiles stay in registers
+// 128 registers per thread where a tile would otherwise spill: two-field
+// kernels (two 256-thread CTAs or one 512-thread CTA per SM) and the
+// 512-thread length-8192 kernels (one CTA per SM; measured at 8192^2: column
+// pass 436 -> 418 us, no spills)
 template <int L, bool TWO>
 __global__ void __launch_bounds__(ColK<L>::THREADS, TWO ? (ColK<L>::THREADS >= 512 ? 1 : 2)
-                                                        : min_blocks<ColK<L>::THREADS>()) k_col_p2(const Desc d) {
+                                                        : (ColK<L>::THREADS >= 512 ? 1 : min_blocks<ColK<L>::THREADS>())) k_col_p2(const Desc d) {
   extern __shared__ __align__(16) unsigned char fs_smem[];
   unit_col_t<float, 16, TWO, L, ColK<L>::CC>(d, blockIdx.x, ColK<L>::CC, reinterpret_cast<cx<float> *>(fs_smem),
                                              reinterpret_cast<cx<float> *>(d.work_u),
@@ -156,7 +158,7 @@ struct ColT {
 };
 
 template <int L>
-__global__ void __launch_bounds__(ColT<L>::THREADS, min_blocks<ColT<L>::THREADS>()) k_col_tma(const Desc d) {
+__global__ void __launch_bounds__(ColT<L>::THREADS, ColT<L>::THREADS >= 512 ? 1 : min_blocks<ColT<L>::THREADS>()) k_col_tma(const Desc d) {
   extern __shared__ __align__(128) unsigned char fs_smem[];
   __shared__ uint64_t bars[2];
   __shared__ int s_abort;
