@@ -139,8 +139,18 @@ def run(n_requests=20000, load=0.8, seed=12312, budget_bytes=150 << 30, slots=3,
         for n in sizes:
             fs.fs_state_destroy(states[n])
             fs.fs_plan_destroy(plans[n])
+    # latency percentiles per grid-size class (where the tail comes from)
+    by_size = {}
+    sizes_arr = np.array([it[2] for it in items])
+    lat_arr, plain_arr = np.asarray(lat, dtype=np.float64), np.asarray(plain_lat, dtype=np.float64)
+    for lo, hi in ((0, 1024), (1025, 4096), (4097, 8192)):
+        m = (sizes_arr >= lo) & (sizes_arr <= hi)
+        if m.any():
+            by_size[f"N{lo}-{hi}"] = {"count": int(m.sum()), "served": _percentiles(lat_arr[m]),
+                                      "plain": _percentiles(plain_arr[m])}
     res = {
         "requests": n_total, "initial_requests": len(base), "load": load,
+        "by_size": by_size,
         "rate_per_s": n_total / (arrivals[-1] - arrivals[0]),
         "served": {"solves_per_s": n_total / makespan, **_percentiles(lat), "batches": stats["batches"],
                    "max_in_flight": stats["max_in_flight"], "peak_hbm_bytes": stats["peak_bytes"]},
