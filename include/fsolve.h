@@ -8,16 +8,24 @@
  *
  * Conventions shared by every entry point
  *   Fields      real, row-major [ny][nx] (x fastest), element type given by
- *               the plan's dtype (float or double), on the DEVICE, owned by the
- *               caller.  Sample x_j = j Lx/nx, y_k = k Ly/ny (Sec. II.D).
+ *               the plan's dtype (float or double), owned by the caller, in
+ *               device memory or in host memory mapped into the device's
+ *               address space (pinned under unified addressing; the kernels
+ *               then read/write it over the host link).  Complex fields
+ *               (the *_c entry points) are interleaved (re, im).
+ *               Sample x_j = j Lx/nx, y_k = k Ly/ny (Sec. II.D).
  *   Wavenumbers omega_x(a) = 2 pi a'/Lx, a' = a for a <= nx/2 else a - nx (the
  *               index shift of Sec. II.B); the Nyquist index is kept with
  *               |omega| = pi nx / Lx.  |omega|^2 = omega_x^2 + omega_y^2.
  *   Sizes       nx, ny even, 8 <= n <= 8192, n = 2^a * {1, 3, 5}; nx != ny and
  *               Lx != Ly allowed.  Anything else: FS_ERR_SIZE.
  *   Streams     fs_stream is a cudaStream_t (NULL = legacy default stream).
- *               Every call only enqueues work on that stream and returns; none
- *               synchronises except fs_serve_poll (bounded by its timeout).
+ *               The solve, advance and batch calls only enqueue work on that
+ *               stream and return.  These wait: fs_batch_wait and
+ *               fs_serve_poll (bounded by their timeouts), fs_state_save/load
+ *               and fs_rk4_mean (the stream), fs_rk4_step (earlier work on the
+ *               stream, before uploading its step table), and the *_destroy
+ *               calls (the device).
  *   Workspace   a plan owns its device workspace (twiddle and wavenumber
  *               tables, one half-spectrum); calls on one plan (or on states of
  *               one plan) must be ordered on one stream.  Different plans are
