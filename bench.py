@@ -210,8 +210,8 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 # of this workload from one ncu capture (profiles/k_batch_diffusion_1024.md),
 # valid only for the CUDA sources it was taken on: any change to them makes
 # the reported traffic null until a new capture.
-TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 247225344 + 794119424,
-                   "sources_sha256": "cef8c33d0c094bde1023ac122b9dff658425b0600e99931e6a67d7fc934b7424"}
+TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 245090304 + 793714944,
+                   "sources_sha256": "857736c9004875eca965e83744dfab13bc0604923591eb47a3e5808ec55100f9"}
 
 
 def _csrc_digest():
