@@ -86,6 +86,35 @@ fs_status fs_plan_destroy(fs_plan plan);
 fs_status fs_plan_info(fs_plan plan, int *nx, int *ny, int *dtype, int *path,
                        size_t *workspace_bytes);
 
+/* ---------------------------------------------------------------- autotuning
+ * fs_tune: time candidate configurations of a grid's standalone passes on the
+ * current GPU (CUDA events, `reps` Poisson solves each after 2 warm-ups; reps
+ * < 1 means 10) and keep the fastest: the register tile (hence the radix
+ * split) of the row and of the column transforms, the row-tile height and the
+ * column-group width.  Rows are tuned first, then columns with the best rows;
+ * the result replaces the default only if it is faster.  The result is stored
+ * in a process-wide cache keyed by (GPU name, nx, ny, dtype) that
+ * fs_plan_create applies to later plans of that grid (a batch adapts the tile
+ * heights to its CTA size), and written to the JSON-lines file named by the
+ * environment variable FS_TUNE_CACHE when it is set (that file is also loaded
+ * on first use).  Grids that run as one single-kernel solve are not tuned
+ * (the default is returned).  Allocates two fields and a stream for the
+ * duration of the call and synchronises them.  No counterpart in the paper.
+ * fs_tune_cache_load/save: read/write the cache as JSON lines; they return
+ * the number of entries, -1 if the file cannot be opened.
+ * fs_tune_cache_clear: drop every entry (returns how many).
+ * fs_plan_tiles: the configuration a plan uses. */
+typedef struct {
+  int e_row, e_col, rows, cols; /* the chosen configuration */
+  double us_default, us_tuned;  /* one Poisson solve, default and chosen */
+  int candidates;               /* configurations timed */
+} fs_tune_result;
+fs_status fs_tune(int nx, int ny, double lx, double ly, int dtype, int reps, fs_tune_result *out);
+int fs_tune_cache_load(const char *path);
+int fs_tune_cache_save(const char *path);
+int fs_tune_cache_clear(void);
+fs_status fs_plan_tiles(fs_plan plan, int *e_row, int *e_col, int *rows, int *cols);
+
 /* ---------------------------------------------------------------- one-shot solves
  * fs_poisson_solve: u = the zero-mean solution of lap u = f - mean(f)
  * (Eq. Poisson2, Eq. SolutionPoisson): forward 2D DFT, multiply by

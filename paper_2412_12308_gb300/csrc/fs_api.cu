@@ -213,6 +213,44 @@ using namespace fs;
 
 static cudaError_t alloc_dev(void **p, size_t bytes) { return cudaMalloc(p, bytes); }
 
+bool fs::make_rp_e(int L, int e, bool f64, RadixPlan *rp) {
+  static const int es_f[] = {4, 5, 6, 8, 10, 12, 16, 20, 24}, es_d[] = {4, 5, 6, 8, 10, 12, 16};
+  bool ok = false;
+  for (int v : (f64 ? std::vector<int>(es_d, es_d + 7) : std::vector<int>(es_f, es_f + 9))) ok |= v == e;
+  if (!ok || L < e || L % e || L / e > kMaxThreads) return false;
+  memset(rp, 0, sizeof *rp);
+  rp->e = e;
+  rp->n = radix_plan(L, e, rp->r, 8);
+  return rp->n > 0;
+}
+
+// Apply a tuned / forced configuration to a plan's geometry; false if it does
+// not fit (the caller keeps the defaults or reports the error).
+static bool apply_cfg(fs_plan_s *t, const TuneCfg &c) {
+  const bool f64 = t->dtype == FS_F64;
+  RadixPlan rr = t->rp_row, rc = t->rp_col;
+  if (c.e_row && !make_rp_e(t->M, c.e_row, f64, &rr)) return false;
+  if (c.e_col && !make_rp_e(t->ny, c.e_col, f64, &rc)) return false;
+  TileConfig tc = make_tiles(t->nx, t->ny, rr, rc, t->csize);
+  tc.rows_per_unit_c = t->tc.rows_per_unit_c;
+  const int tr = t->M / rr.e, tcl = t->ny / rc.e;
+  const size_t lim = 200 * 1024;
+  if (c.rows) {
+    const bool p2 = t->csize == 8 && rr.e == 16 && p2_row_ok(t->M) && c.rows == p2_row_cnt(t->M);
+    if (c.rows > t->ny || c.rows * tr > (p2 ? 1024 : kMaxThreads) || t->csize * padded_len(c.rows * t->M) > lim)
+      return false;
+    tc.rows_per_unit = c.rows;
+  }
+  if (c.cols) {
+    if (c.cols * tcl > kMaxThreads || t->csize * padded_len(c.cols * t->ny) > lim) return false;
+    tc.cols_per_unit = c.cols;
+  }
+  t->rp_row = rr;
+  t->rp_col = rc;
+  t->tc = tc;
+  return true;
+}
+
 static fs_status ensure_work_v(fs_plan p) {
   if (p->work_v) return FS_OK;
   cudaError_t e = alloc_dev(&p->work_v, p->spec_bytes);
@@ -243,6 +281,13 @@ fs_status fs_device_status(int *code) {
 }
 
 fs_status fs_plan_create(int nx, int ny, double lx, double ly, int dtype, fs_plan *out) {
+  return plan_create_cfg(nx, ny, lx, ly, dtype, nullptr, out);
+}
+
+}  // extern "C"
+
+fs_status fs::plan_create_cfg(int nx, int ny, double lx, double ly, int dtype, const TuneCfg *force,
+                              fs_plan *out) {
   if (!out) return set_error(FS_ERR_ARG, "fs_plan_create: out is NULL");
   *out = nullptr;
   if (!(lx > 0.0) || !(ly > 0.0) || !std::isfinite(lx) || !std::isfinite(ly))
@@ -288,6 +333,17 @@ fs_status fs_plan_create(int nx, int ny, double lx, double ly, int dtype, fs_pla
   }
   e = cudaGetDevice(&tmp.device);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  // tuned configuration: forced (tuner candidates) or from the cache
+  {
+    TuneCfg cfg{};
+    if (force) {
+      if (!apply_cfg(&tmp, *force)) return set_error(FS_ERR_ARG, "fs_plan_create: configuration does not fit");
+    } else if (tune_lookup(tmp.device, nx, ny, dtype, &cfg)) {
+      fs_plan_s keep = tmp;
+      if (!apply_cfg(&tmp, cfg)) tmp = keep;  // a stale entry: keep the defaults
+    }
+    tmp.standalone_small = (nx * ny <= small_max) && tmp.tc.small_smem2 > 0;
+  }
 
   // ---- host tables in FP64
   const bool f64 = dtype == FS_F64;
@@ -363,6 +419,17 @@ fs_status fs_plan_create(int nx, int ny, double lx, double ly, int dtype, fs_pla
     return cuda_error(e, "fs_plan_create: table upload");
   }
   *out = p;
+  return FS_OK;
+}
+
+extern "C" {
+
+fs_status fs_plan_tiles(fs_plan p, int *e_row, int *e_col, int *rows, int *cols) {
+  if (!p) return set_error(FS_ERR_ARG, "fs_plan_tiles: plan is NULL");
+  if (e_row) *e_row = p->rp_row.e;
+  if (e_col) *e_col = p->rp_col.e;
+  if (rows) *rows = p->tc.rows_per_unit;
+  if (cols) *cols = p->tc.cols_per_unit;
   return FS_OK;
 }
 

@@ -59,6 +59,18 @@ struct fs_state_s {
 };
 
 namespace fs {
+// A tuned configuration of a grid's passes (0 = the default): register tile
+// (hence radix split) of the row and column transforms, row-tile height and
+// column-group width of the standalone pass kernels.
+struct TuneCfg {
+  int e_row, e_col, rows, cols;
+};
+// The tuning cache (fs_tune.cu): configurations by (GPU name, nx, ny, dtype).
+bool tune_lookup(int device, int nx, int ny, int dtype, TuneCfg *out);
+// Plan creation with a forced configuration (nullptr: the cache, else defaults).
+fs_status plan_create_cfg(int nx, int ny, double lx, double ly, int dtype, const TuneCfg *force, fs_plan *out);
+// Radix plan of a length-L transform with register tile e (false: not available).
+bool make_rp_e(int L, int e, bool f64, RadixPlan *rp);
 // Radix plans and tile shapes for an nx x ny grid (false: unsupported size).
 bool plan_geometry(int nx, int ny, bool f64, RadixPlan *rr, RadixPlan *rc, TileConfig *tc);
 // Descriptor with the plan's geometry, tables and tile shapes filled in.

@@ -48,6 +48,13 @@ class FsOrbitSource(ctypes.Structure):
                 ("y_min", ctypes.c_double)]
 
 
+class FsTuneResult(ctypes.Structure):
+    """fs_tune_result of include/fsolve.h."""
+
+    _fields_ = [("e_row", ctypes.c_int), ("e_col", ctypes.c_int), ("rows", ctypes.c_int), ("cols", ctypes.c_int),
+                ("us_default", ctypes.c_double), ("us_tuned", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
 # Entry points declared in include/fsolve.h: name -> (restype, argtypes)
 _SIGS = {
     "fs_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -56,6 +63,13 @@ _SIGS = {
     "fs_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_size_t)]),
+    "fs_tune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                               ctypes.c_int, ctypes.POINTER(FsTuneResult)]),
+    "fs_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "fs_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "fs_tune_cache_clear": (ctypes.c_int, []),
+    "fs_plan_tiles": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "fs_poisson_solve": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "fs_poisson_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                _vp, _vp, _vp]),
@@ -204,6 +218,37 @@ def fs_wave_solve(plan, u0, v0, c, t, u, stream=None):
     load()
     _check(_lib.fs_wave_solve(plan, _ptr(u0), _ptr(v0), float(c), float(t), _ptr(u), _stream(stream)),
            "fs_wave_solve")
+
+
+def fs_tune(nx, ny, lx, ly, dtype, reps=10):
+    """Autotune a grid's passes on this GPU; returns the chosen configuration."""
+    load()
+    r = FsTuneResult()
+    _check(_lib.fs_tune(int(nx), int(ny), float(lx), float(ly), int(dtype), int(reps), ctypes.byref(r)), "fs_tune")
+    return {k: getattr(r, k) for k, _ in FsTuneResult._fields_}
+
+
+def fs_tune_cache_load(path):
+    load()
+    return _lib.fs_tune_cache_load(os.fsencode(path))
+
+
+def fs_tune_cache_save(path):
+    load()
+    return _lib.fs_tune_cache_save(os.fsencode(path))
+
+
+def fs_tune_cache_clear():
+    load()
+    return _lib.fs_tune_cache_clear()
+
+
+def fs_plan_tiles(plan):
+    """(e_row, e_col, rows, cols) of a plan."""
+    load()
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(_lib.fs_plan_tiles(plan, *[ctypes.byref(x) for x in v]), "fs_plan_tiles")
+    return tuple(x.value for x in v)
 
 
 def fs_poisson_solve_c(plan, f, u, stream=None):

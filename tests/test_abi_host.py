@@ -123,3 +123,25 @@ def test_batch_rejects_bad_requests_on_host(lib):
     t = ctypes.c_uint64()
     assert lib.fs_batch_submit(arr, 1, ctypes.byref(t), None) == -1  # no plan
     assert lib.fs_batch_wait(12345678, 0) == -1  # unknown ticket
+
+
+def test_tune_cache_file_roundtrip(lib, tmp_path):
+    """The autotuner's cache is JSON lines keyed by (gpu, nx, ny, dtype): load
+    skips lines that are not entries, save writes every entry back."""
+    src = tmp_path / "in.jsonl"
+    src.write_text(
+        '{"gpu": "NVIDIA GB300", "nx": 4096, "ny": 4096, "dtype": 0, "e_row": 16, "e_col": 16, "rows": 4, '
+        '"cols": 1, "us": 186.2}\n'
+        'not json at all\n'
+        '{"gpu": "NVIDIA GB300", "nx": 1536, "ny": 1536, "dtype": 1, "e_row": 12, "e_col": 12, "rows": 8, '
+        '"cols": 2, "us": 900.5}\n'
+        '{"gpu": "NVIDIA GB300", "nx": 64}\n')
+    lib.fs_tune_cache_clear()
+    assert lib.fs_tune_cache_load(str(src).encode()) == 2
+    dst = tmp_path / "out.jsonl"
+    assert lib.fs_tune_cache_save(str(dst).encode()) == 2
+    lines = sorted(dst.read_text().strip().splitlines())
+    assert len(lines) == 2 and '"nx": 1536' in lines[0] and '"e_row": 12' in lines[0] and '"rows": 4' in lines[1]
+    assert lib.fs_tune_cache_load(str(tmp_path / "missing.jsonl").encode()) == -1
+    assert lib.fs_tune_cache_clear() == 2
+
