@@ -110,6 +110,15 @@ typedef struct {
   int candidates;               /* configurations timed */
 } fs_tune_result;
 fs_status fs_tune(int nx, int ny, double lx, double ly, int dtype, int reps, fs_tune_result *out);
+/* fs_tune_batch: the same for a grid run inside a batch: times `nprob`
+ * Poisson solves of the grid in one fs_batch_submit (after two warm-ups) for
+ * every pair of row / column register tiles, and stores the fastest pair
+ * under the batch mode of the cache (tile heights in a batch follow its CTA
+ * size).  fs_batch_submit applies it to problems of that grid that run as
+ * units (not the single-CTA or standalone ones).  rows/cols of the result
+ * are 0. */
+fs_status fs_tune_batch(int nx, int ny, double lx, double ly, int dtype, int nprob, int reps,
+                        fs_tune_result *out);
 int fs_tune_cache_load(const char *path);
 int fs_tune_cache_save(const char *path);
 int fs_tune_cache_clear(void);

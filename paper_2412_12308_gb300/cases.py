@@ -224,7 +224,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--f64", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="autotune every grid of the case first (fs_tune)")
     a = ap.parse_args()
+    if a.tune:
+        from . import fsolve, workloads
+
+        fsolve.load()
+        if a.case == "batch_mix":  # the batch's own tuning, per grid of the mix
+            for n in sorted({p.n for p in workloads.batch_mix()}):
+                if n * n > 256 * 256:  # smaller grids run as single-CTA problems
+                    fsolve.fs_tune_batch(n, n, 1.0, 1.0, 0, nprob=8, reps=3)
+        else:
+            fsolve.fs_tune(a.n, a.n, 1.0, 1.0, 1 if a.f64 else 0, reps=5)
     print(json.dumps(run(a.case, a.n, a.iters, a.warmup, 1 if a.f64 else 0, not a.no_profile)))
 
 

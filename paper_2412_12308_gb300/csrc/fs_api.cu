@@ -338,7 +338,7 @@ fs_status fs::plan_create_cfg(int nx, int ny, double lx, double ly, int dtype, c
     TuneCfg cfg{};
     if (force) {
       if (!apply_cfg(&tmp, *force)) return set_error(FS_ERR_ARG, "fs_plan_create: configuration does not fit");
-    } else if (tune_lookup(tmp.device, nx, ny, dtype, &cfg)) {
+    } else if (tune_lookup(tmp.device, nx, ny, dtype, 0, &cfg)) {
       fs_plan_s keep = tmp;
       if (!apply_cfg(&tmp, cfg)) tmp = keep;  // a stale entry: keep the defaults
     }

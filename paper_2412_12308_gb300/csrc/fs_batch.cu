@@ -192,6 +192,18 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
     const size_t small_b = nspec == 2 ? p->tc.small_smem2 : p->tc.small_smem1;
     const long long small_max = env_ll("FS_BATCH_SMALL_MAX", 256LL * 256LL);
     d.small = (small_b > 0 && small_b <= kMaxDynSmem && (long long)p->nx * p->ny <= small_max) ? 1 : 0;
+    // batch-mode tuned register tiles (fs_tune_batch) for problems run as units
+    if (!d.small && !(direct_min_points > 0 && (long long)p->nx * p->ny >= direct_min_points)) {
+      TuneCfg tc{};
+      if (tune_lookup(p->device, p->nx, p->ny, p->dtype, 1, &tc)) {
+        RadixPlan rr, rc;
+        const bool f64 = p->dtype == FS_F64;
+        if (tc.e_row && make_rp_e(d.M, tc.e_row, f64, &rr) && tc.e_col && make_rp_e(d.ny, tc.e_col, f64, &rc)) {
+          d.rp_row = rr;
+          d.rp_col = rc;
+        }
+      }
+    }
     size_t ws = 0;
     if (diff) ws += align256(fac_bytes(p));
     if (!d.small) {

@@ -65,8 +65,10 @@ namespace fs {
 struct TuneCfg {
   int e_row, e_col, rows, cols;
 };
-// The tuning cache (fs_tune.cu): configurations by (GPU name, nx, ny, dtype).
-bool tune_lookup(int device, int nx, int ny, int dtype, TuneCfg *out);
+// The tuning cache (fs_tune.cu): configurations by (GPU name, nx, ny, dtype,
+// mode); mode 0 = standalone passes (plan creation), 1 = inside a batch (only
+// the register tiles apply there).
+bool tune_lookup(int device, int nx, int ny, int dtype, int mode, TuneCfg *out);
 // Plan creation with a forced configuration (nullptr: the cache, else defaults).
 fs_status plan_create_cfg(int nx, int ny, double lx, double ly, int dtype, const TuneCfg *force, fs_plan *out);
 // Radix plan of a length-L transform with register tile e (false: not available).

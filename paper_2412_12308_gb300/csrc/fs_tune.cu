@@ -25,7 +25,7 @@ using namespace fs;
 
 namespace {
 
-typedef std::tuple<std::string, int, int, int> Key;  // GPU name, nx, ny, dtype
+typedef std::tuple<std::string, int, int, int, int> Key;  // GPU name, nx, ny, dtype, mode
 struct Entry {
   TuneCfg cfg;
   double us;
@@ -74,14 +74,15 @@ int load_locked(const char *path) {
   while (fgets(buf, sizeof buf, f)) {
     const std::string line(buf);
     std::string gpu;
-    double nx, ny, dt, er, ec, rows, cols, us = 0.0;
+    double nx, ny, dt, er, ec, rows, cols, us = 0.0, mode = 0.0;
     if (!field_str(line, "gpu", &gpu) || !field_num(line, "nx", &nx) || !field_num(line, "ny", &ny) ||
         !field_num(line, "dtype", &dt) || !field_num(line, "e_row", &er) || !field_num(line, "e_col", &ec) ||
         !field_num(line, "rows", &rows) || !field_num(line, "cols", &cols))
       continue;  // not an entry
     field_num(line, "us", &us);
+    field_num(line, "mode", &mode);  // absent: standalone
     Entry e{{(int)er, (int)ec, (int)rows, (int)cols}, us};
-    g_cache[Key(gpu, (int)nx, (int)ny, (int)dt)] = e;
+    g_cache[Key(gpu, (int)nx, (int)ny, (int)dt, (int)mode)] = e;
     ++n;
   }
   fclose(f);
@@ -96,10 +97,10 @@ int save_locked(const char *path) {
     const Key &k = kv.first;
     const Entry &e = kv.second;
     fprintf(f,
-            "{\"gpu\": \"%s\", \"nx\": %d, \"ny\": %d, \"dtype\": %d, \"e_row\": %d, \"e_col\": %d, "
-            "\"rows\": %d, \"cols\": %d, \"us\": %.3f}\n",
-            std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k), e.cfg.e_row, e.cfg.e_col,
-            e.cfg.rows, e.cfg.cols, e.us);
+            "{\"gpu\": \"%s\", \"nx\": %d, \"ny\": %d, \"dtype\": %d, \"mode\": %d, \"e_row\": %d, "
+            "\"e_col\": %d, \"rows\": %d, \"cols\": %d, \"us\": %.3f}\n",
+            std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), e.cfg.e_row,
+            e.cfg.e_col, e.cfg.rows, e.cfg.cols, e.us);
     ++n;
   }
   fclose(f);
@@ -142,11 +143,18 @@ double time_cfg(int nx, int ny, double lx, double ly, int dtype, const TuneCfg &
 
 }  // namespace
 
-bool fs::tune_lookup(int device, int nx, int ny, int dtype, TuneCfg *out) {
+// candidate forced on the batch planner by fs_tune_batch (this thread only)
+thread_local const TuneCfg *t_force_batch = nullptr;
+
+bool fs::tune_lookup(int device, int nx, int ny, int dtype, int mode, TuneCfg *out) {
+  if (mode == 1 && t_force_batch) {
+    *out = *t_force_batch;
+    return true;
+  }
   std::lock_guard<std::mutex> g(g_mu);
   env_load_locked();
   if (g_cache.empty()) return false;
-  auto it = g_cache.find(Key(gpu_name(device), nx, ny, dtype));
+  auto it = g_cache.find(Key(gpu_name(device), nx, ny, dtype, mode));
   if (it == g_cache.end()) return false;
   *out = it->second.cfg;
   return true;
@@ -243,10 +251,108 @@ fs_status fs_tune(int nx, int ny, double lx, double ly, int dtype, int reps, fs_
   {
     std::lock_guard<std::mutex> g(g_mu);
     env_load_locked();
-    g_cache[Key(gpu_name(device), nx, ny, dtype)] =
+    g_cache[Key(gpu_name(device), nx, ny, dtype, 0)] =
         Entry{{res->e_row, res->e_col, res->rows, res->cols}, us_best};
     if (const char *path = getenv("FS_TUNE_CACHE")) save_locked(path);
   }
+  return FS_OK;
+}
+
+fs_status fs_tune_batch(int nx, int ny, double lx, double ly, int dtype, int nprob, int reps, fs_tune_result *res) {
+  if (!res) return set_error(FS_ERR_ARG, "fs_tune_batch: result is NULL");
+  memset(res, 0, sizeof *res);
+  if (reps < 1) reps = 5;
+  if (nprob < 1) nprob = 8;
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_error(e, "fs_tune_batch");
+  fs_plan p = nullptr;
+  fs_status st = plan_create_cfg(nx, ny, lx, ly, dtype, nullptr, &p);
+  if (st != FS_OK) return st;
+  const size_t bytes = (size_t)nx * ny * (dtype == FS_F64 ? sizeof(double) : sizeof(float));
+  void *f = nullptr, *u = nullptr;
+  cudaStream_t s = nullptr;
+  e = cudaMalloc(&f, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&u, bytes * (size_t)nprob);
+  if (e == cudaSuccess) e = cudaMemset(f, 0x3c, bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaFree(f);
+    cudaFree(u);
+    fs_plan_destroy(p);
+    return cuda_error(e, "fs_tune_batch: buffers");
+  }
+  std::vector<fs_request> reqs(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    memset(&reqs[i], 0, sizeof(fs_request));
+    reqs[i].op = FS_OP_POISSON;
+    reqs[i].plan = p;
+    reqs[i].in_u = f;
+    reqs[i].out_u = static_cast<char *>(u) + bytes * (size_t)i;
+  }
+  auto time_batch = [&](const TuneCfg *c) -> double {
+    t_force_batch = c;
+    double us = -1.0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    uint64_t tk = 0;
+    for (int i = 0; i < 2 && ok; ++i)  // warm-up (graph capture)
+      ok = fs_batch_submit(reqs.data(), nprob, &tk, s) == FS_OK && fs_batch_wait(tk, 60000000) == FS_OK;
+    if (ok) {
+      cudaEventRecord(a, s);
+      for (int i = 0; i < reps && ok; ++i) ok = fs_batch_submit(reqs.data(), nprob, &tk, s) == FS_OK;
+      cudaEventRecord(b, s);
+      float ms = 0.f;
+      if (ok && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+        us = 1e3 * ms / reps;
+      if (ok) fs_batch_wait(tk, 60000000);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaStreamSynchronize(s);
+    t_force_batch = nullptr;
+    return us;
+  };
+  const TuneCfg none{0, 0, 0, 0};
+  const double us_default = time_batch(&none);
+  TuneCfg best = none;
+  double us_best = us_default;
+  int cand = 1;
+  if (us_default < 0.0) st = set_error(FS_ERR_SIZE, "fs_tune_batch: the default configuration does not run");
+  static const int es_f[] = {4, 5, 6, 8, 10, 12, 16, 20, 24}, es_d[] = {4, 5, 6, 8, 10, 12, 16};
+  const int *elist = dtype == FS_F64 ? es_d : es_f;
+  const int ne = dtype == FS_F64 ? 7 : 9;
+  for (int i = 0; i < ne && st == FS_OK; ++i) {
+    RadixPlan rr;
+    if (!make_rp_e(nx / 2, elist[i], dtype == FS_F64, &rr)) continue;
+    for (int j = 0; j < ne; ++j) {
+      RadixPlan rc;
+      if (!make_rp_e(ny, elist[j], dtype == FS_F64, &rc)) continue;
+      if (rr.e == p->rp_row.e && rc.e == p->rp_col.e) continue;  // the default, timed above
+      const TuneCfg c{elist[i], elist[j], 0, 0};
+      const double us = time_batch(&c);
+      if (us < 0.0) continue;
+      ++cand;
+      if (us < us_best) {
+        us_best = us;
+        best = c;
+      }
+    }
+  }
+  cudaStreamDestroy(s);
+  cudaFree(f);
+  cudaFree(u);
+  res->e_row = best.e_row ? best.e_row : p->rp_row.e;
+  res->e_col = best.e_col ? best.e_col : p->rp_col.e;
+  fs_plan_destroy(p);
+  if (st != FS_OK) return st;
+  res->us_default = us_default;
+  res->us_tuned = us_best;
+  res->candidates = cand;
+  std::lock_guard<std::mutex> g(g_mu);
+  env_load_locked();
+  g_cache[Key(gpu_name(device), nx, ny, dtype, 1)] = Entry{{res->e_row, res->e_col, 0, 0}, us_best};
+  if (const char *path = getenv("FS_TUNE_CACHE")) save_locked(path);
   return FS_OK;
 }
 

@@ -65,6 +65,8 @@ _SIGS = {
                                     ctypes.POINTER(ctypes.c_size_t)]),
     "fs_tune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                ctypes.c_int, ctypes.POINTER(FsTuneResult)]),
+    "fs_tune_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.POINTER(FsTuneResult)]),
     "fs_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
     "fs_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
     "fs_tune_cache_clear": (ctypes.c_int, []),
@@ -225,6 +227,15 @@ def fs_tune(nx, ny, lx, ly, dtype, reps=10):
     load()
     r = FsTuneResult()
     _check(_lib.fs_tune(int(nx), int(ny), float(lx), float(ly), int(dtype), int(reps), ctypes.byref(r)), "fs_tune")
+    return {k: getattr(r, k) for k, _ in FsTuneResult._fields_}
+
+
+def fs_tune_batch(nx, ny, lx, ly, dtype, nprob=8, reps=5):
+    """Autotune a grid's register tiles inside a batch; returns the chosen pair."""
+    load()
+    r = FsTuneResult()
+    _check(_lib.fs_tune_batch(int(nx), int(ny), float(lx), float(ly), int(dtype), int(nprob), int(reps),
+                              ctypes.byref(r)), "fs_tune_batch")
     return {k: getattr(r, k) for k, _ in FsTuneResult._fields_}
 
 

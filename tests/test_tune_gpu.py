@@ -67,3 +67,31 @@ def test_tune_cache_file_and_stale_entry(clean_cache, tmp_path):
     p = fs.fs_plan_create(n, n, 1.0, 1.0, 0)
     assert fs.fs_plan_tiles(p) == d_tiles
     fs.fs_plan_destroy(p)
+
+
+@pytest.mark.parametrize("n", [384, 640])
+def test_tune_batch_and_use(clean_cache, n):
+    """Batch-mode tuning picks register tiles for the grid inside a batch; a
+    batch using them still matches the closed form for every problem."""
+    r = fs.fs_tune_batch(n, n, 1.0, 1.0, 0, nprob=4, reps=2)
+    assert r["candidates"] >= 1 and 0 < r["us_tuned"] <= r["us_default"] * 1.0001
+    plan = fs.fs_plan_create(n, n, 1.0, 1.0, 0)
+    try:
+        rng = np.random.default_rng(n + 3)
+        fields, outs, reqs, wants = [], [], [], []
+        for _ in range(6):
+            modes = wl.draw_modes(rng, 8, 30)
+            f = torch.tensor(wl.mode_sum(modes, n, n, 1.0, 1.0), dtype=torch.float32, device="cuda")
+            o = torch.empty_like(f)
+            fields.append(f)
+            outs.append(o)
+            wants.append(cf.poisson_modes(modes, n, n, 1.0, 1.0))
+            reqs.append(fs.fs_request(fs.FS_OP_POISSON, plan=plan, in_u=f, out_u=o))
+        fs.fs_batch_wait(fs.fs_batch_submit(reqs), 30_000_000)
+        torch.cuda.synchronize()
+        for o, want in zip(outs, wants):
+            got = o.double().cpu().numpy()
+            assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-5
+    finally:
+        fs.fs_plan_destroy(plan)
+
