@@ -518,14 +518,20 @@ template <typename T>
 static cudaError_t run_complex_desc(const Desc &d, cudaStream_t s) {
   typedef Launch<T> L;
   const PassKernels pk = pass_kernels<T>(d.rp_row.e);
+  PassKernel kf = pk.c2cf, ki = pk.c2ci;
+  // FP32 power-of-two rows: the compile-time kernels when the tile matches
+  if (sizeof(T) == 4 && d.rp_row.e == 16 && p2_c2c_ok(d.nx) && d.rows_per_unit == p2_c2c_cnt(d.nx)) {
+    kf = p2_c2c_f32(d.nx, false);
+    ki = p2_c2c_f32(d.nx, true);
+  }
   const int threads = round_up32(d.rows_per_unit * (d.nx / d.rp_row.e));
   const size_t smem = sizeof(cx<T>) * (size_t)padded_len(d.rows_per_unit * d.nx);
   const int fields = (d.op == OP_WAVE && (d.flags & F_HAS_V0)) ? 2 : 1;
   cudaError_t e = cudaSuccess;
   if (d.op == OP_DIFFUSION) e = L::factor(d, s);
-  if (e == cudaSuccess) e = L::launch(pk.c2cf, d.n_row_units * fields, threads, smem, d, s, PC_R2C);
+  if (e == cudaSuccess) e = L::launch(kf, d.n_row_units * fields, threads, smem, d, s, PC_R2C);
   if (e == cudaSuccess) e = L::cols(d, s);
-  if (e == cudaSuccess) e = L::launch(pk.c2ci, d.n_row_units, threads, smem, d, s, PC_C2R);
+  if (e == cudaSuccess) e = L::launch(ki, d.n_row_units, threads, smem, d, s, PC_C2R);
   return e;
 }
 

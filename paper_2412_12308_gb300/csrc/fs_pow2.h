@@ -17,6 +17,9 @@ constexpr int p2_row_cnt(int M) {
   return (M / 16) >= 256 ? 2 : ((M / 16) * 16 <= 512 ? 16 : 512 / (M / 16));
 }
 constexpr bool p2_row_ok(int M) { return M >= 128 && M <= 4096 && (M & (M - 1)) == 0; }
+// Complex (C2C) rows of length N: up to 16 rows and 512 threads per CTA.
+constexpr int p2_c2c_cnt(int N) { return (N / 16) * 16 <= 512 ? 16 : 512 / (N / 16); }
+constexpr bool p2_c2c_ok(int N) { return N >= 128 && N <= 8192 && (N & (N - 1)) == 0; }
 
 // Device-side unit functions for the persistent batch and single-CTA paths
 // (row tiles must use p2_row_cnt(M) rows; columns take any count).  Return
@@ -38,6 +41,7 @@ PassKernel p2_c2r_f32(int M);
 PassKernel p2_col1_f32(int L);
 PassKernel p2_col2_f32(int L);
 PassKernel p2_cols_f32(int L, bool two);  // advances with a constant source
+PassKernel p2_c2c_f32(int N, bool inverse);  // complex rows, forward / inverse
 // TMA-staged persistent column kernel (single field) and its shared memory.
 PassKernel p2_col_tma_f32(int L);
 // Split-BF16 tensor-core first stage (measured variant, FS_COLUMN_VARIANT=bf16x3).

@@ -66,6 +66,31 @@ __global__ void __launch_bounds__(ColK<L>::THREADS, TWO ? (ColK<L>::THREADS >= 5
                                              reinterpret_cast<cx<float> *>(d.work_v), false);
 }
 
+// ---------------------------------------------------------------- complex rows
+template <int N>
+struct C2CK {
+  static constexpr int CC = p2_c2c_cnt(N);
+  static constexpr int THREADS = CC * (N / 16);
+};
+template <int N>
+__global__ void __launch_bounds__(C2CK<N>::THREADS, min_blocks<C2CK<N>::THREADS>()) k_c2cf_p2(const Desc d) {
+  extern __shared__ __align__(16) unsigned char fs_smem[];
+  int unit = blockIdx.x;
+  const bool second = unit >= d.n_row_units;
+  if (second) unit -= d.n_row_units;
+  unit_row_c2c_t<float, 16, N, C2CK<N>::CC>(d, unit, C2CK<N>::CC, reinterpret_cast<cx<float> *>(fs_smem),
+                                            reinterpret_cast<const cx<float> *>(second ? d.in_v : d.in_u),
+                                            reinterpret_cast<cx<float> *>(second ? d.work_v : d.work_u),
+                                            nullptr, false);
+}
+template <int N>
+__global__ void __launch_bounds__(C2CK<N>::THREADS, min_blocks<C2CK<N>::THREADS>()) k_c2ci_p2(const Desc d) {
+  extern __shared__ __align__(16) unsigned char fs_smem[];
+  unit_row_c2c_t<float, 16, N, C2CK<N>::CC>(d, blockIdx.x, C2CK<N>::CC, reinterpret_cast<cx<float> *>(fs_smem),
+                                            nullptr, reinterpret_cast<cx<float> *>(d.work_u),
+                                            reinterpret_cast<cx<float> *>(d.out_u), true);
+}
+
 // ---------------------------------------------------------------- TMA column pass
 // Persistent CTAs walk column groups a = blockIdx.x*CC, += gridDim.x*CC.  The
 // CC columns of a group are one contiguous run of the x-frequency-major
@@ -277,6 +302,18 @@ PassKernel p2_col1_f32(int L) {
       return nullptr;
   }
 }
+PassKernel p2_c2c_f32(int N, bool inverse) {
+  switch (N) {
+#define C(n) \
+  case n:    \
+    return inverse ? k_c2ci_p2<n> : k_c2cf_p2<n>;
+    C(128) C(256) C(512) C(1024) C(2048) C(4096) C(8192)
+#undef C
+    default:
+      return nullptr;
+  }
+}
+
 PassKernel p2_col_tma_f32(int L) {
   switch (L) {
 #define C(l) \

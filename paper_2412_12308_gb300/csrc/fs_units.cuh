@@ -134,10 +134,12 @@ __device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt_
 // length-nx plan is d.rp_row of the complex descriptor.  The inverse runs by
 // conjugation (conj of the forward DFT of conj); no scaling (1/(nx ny) is in
 // the spectral multiplier).
-template <typename T, int E>
-__device__ __forceinline__ void unit_row_c2c_t(const Desc &d, int unit, int cnt, cx<T> *sm, const cx<T> *in,
+// NC, CC: compile-time row length and rows per tile (0 = from d / cnt_rt).
+template <typename T, int E, int NC = 0, int CC = 0>
+__device__ __forceinline__ void unit_row_c2c_t(const Desc &d, int unit, int cnt_rt, cx<T> *sm, const cx<T> *in,
                                                cx<T> *spec, cx<T> *out, bool inverse) {
-  const int N = d.nx, ny = d.ny, Tseg = N / E;
+  const int N = NC ? NC : d.nx, ny = d.ny, Tseg = N / E;
+  const int cnt = CC ? CC : cnt_rt;
   const int tid = threadIdx.x;
   const int t = tid / cnt, rho = tid - t * cnt;
   const int y = unit * cnt + rho;
@@ -158,7 +160,7 @@ __device__ __forceinline__ void unit_row_c2c_t(const Desc &d, int unit, int cnt,
 #pragma unroll
     for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();
   }
-  fft_any<T, E, 0, 0, 1>(v, sm, lay, active, t, Tseg, N, d.rp_row, tw);
+  fft_any<T, E, NC, CC, 1>(v, sm, lay, active, t, Tseg, N, d.rp_row, tw);
   if (active) {
     if (inverse) {
       cx<T> *row = out + (size_t)y * N;
