@@ -210,8 +210,8 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 # of this workload from one ncu capture (profiles/k_batch_diffusion_1024.md),
 # valid only for the CUDA sources it was taken on: any change to them makes
 # the reported traffic null until a new capture.
-TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 245090304 + 793714944,
-                   "sources_sha256": "857736c9004875eca965e83744dfab13bc0604923591eb47a3e5808ec55100f9"}
+TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 244096512 + 794661376,
+                   "sources_sha256": "078c3307172715579b4d98ffab783843557bc90d8f375ac2b19fa887ea841759"}
 
 
 def _csrc_digest():
