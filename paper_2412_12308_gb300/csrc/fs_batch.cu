@@ -268,10 +268,21 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
       if (cc < 1) cc = 1;
       while (cc > 1 && (size_t)padded_len(cc * d.ny) * cs > 100 * 1024) cc >>= 1;
       d.cols_per_unit = cc;
+      // single-field FP32 power-of-two columns: each column group is staged
+      // into shared memory by one bulk copy while the previous one computes
+      if (bp->dtype == FS_F32 && !d.small && d.rp_col.e == 16 && p2_col_ok(d.ny) && !col_two_fields(d) &&
+          !(d.flags & F_SOURCE) && tma_enabled())
+        d.flags |= F_COL_TMA;
       int rr = d.rows_per_unit;  // the plan's row tile
       if (rr * tr > bp->threads) rr = std::max(1, bp->threads / tr);
       d.rows_per_unit = rr;
       d.n_row_units = (d.ny + rr - 1) / rr;
+      // C2R tiles of an even number of FP32 power-of-two rows: each tile is
+      // staged into shared memory by asynchronous copies while the previous
+      // one computes
+      if (bp->dtype == FS_F32 && !d.small && d.rp_row.e == 16 && p2_row_ok(d.M) && rr % 2 == 0 &&
+          (rr == p2_row_cnt(d.M) || rr == p2_row_cnt_256(d.M)) && tma_enabled())
+        d.flags |= F_ROW_STAGED;
       d.n_col_units = (d.M + 1 + cc - 1) / cc;
       if (d.small) {
         if (d.small_rows * tr > bp->threads) d.small_rows = std::max(1, bp->threads / tr);
@@ -361,7 +372,10 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
 template <typename T>
 static size_t unit_smem(const Desc &d) {
   if (d.small) return Launch<T>::small_smem(d);
-  return std::max(Launch<T>::row_smem(d), Launch<T>::col_smem(d));
+  const size_t col = (d.flags & F_COL_TMA) ? p2_col1_tma_unit_smem(d.ny, d.cols_per_unit) : Launch<T>::col_smem(d);
+  const size_t row = (d.flags & F_ROW_STAGED) ? 2 * (size_t)c2r_stage_len(d.M, d.rows_per_unit) * sizeof(cx<T>)
+                                               : Launch<T>::row_smem(d);
+  return std::max(row, col);
 }
 
 // A problem run as standalone pass kernels (the per-call path) with the

@@ -4,7 +4,10 @@
 #pragma once
 #include <atomic>
 
+#include "fs_col_tma.cuh"
 #include "fs_pow2.h"
+#include "fs_row_async.cuh"
+#include "fs_tma.cuh"
 #include "fs_units.cuh"
 
 namespace fs {
@@ -73,6 +76,31 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+// Batch column unit staged by bulk copies (F_COL_TMA): columns [c0, c1) in
+// groups of cnt, the second group buffer after the first in `sm`.  Inlined
+// (a call would keep the shared-memory descriptor's fields live across the
+// ABI boundary and spill).  Returns 1 done, 0 length not specialised, -1 a
+// copy timed out.
+template <int L>
+__device__ __forceinline__ int col_tma_unit_l(const Desc &d, int c0, int c1, int cnt, cx<float> *sm,
+                                              uint64_t *bars, uint32_t &ph, int *s_abort) {
+  const int plen = (padded_len(cnt * L) + 1) & ~1;  // even: the second buffer stays 16-byte aligned
+  return col_tma_groups<L, 0>(d, c0, cnt, c1, cnt, sm, sm + plen, bars, ph, s_abort) ? 1 : -1;
+}
+__device__ __forceinline__ int col_tma_unit(const Desc &d, int c0, int c1, int cnt, cx<float> *sm, uint64_t *bars,
+                                            uint32_t &ph, int *s_abort) {
+  switch (d.ny) {
+    case 128: return col_tma_unit_l<128>(d, c0, c1, cnt, sm, bars, ph, s_abort);
+    case 256: return col_tma_unit_l<256>(d, c0, c1, cnt, sm, bars, ph, s_abort);
+    case 512: return col_tma_unit_l<512>(d, c0, c1, cnt, sm, bars, ph, s_abort);
+    case 1024: return col_tma_unit_l<1024>(d, c0, c1, cnt, sm, bars, ph, s_abort);
+    case 2048: return col_tma_unit_l<2048>(d, c0, c1, cnt, sm, bars, ph, s_abort);
+    case 4096: return col_tma_unit_l<4096>(d, c0, c1, cnt, sm, bars, ph, s_abort);
+    case 8192: return col_tma_unit_l<8192>(d, c0, c1, cnt, sm, bars, ph, s_abort);
+    default: return 0;
+  }
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -92,7 +120,16 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1) k_batch(const
   __shared__ int s_unit, s_abort;
   cx<T> *sm = reinterpret_cast<cx<T> *>(fs_smem);
   __shared__ int s_next;
-  if (threadIdx.x == 0) s_next = atomicAdd(&ctl[0], 1);
+  // mbarriers of the bulk-copy column units (F_COL_TMA); ph = their next
+  // completion parities, identical in every thread
+  __shared__ uint64_t s_bars[2];
+  uint32_t tma_ph = 0;
+  if (threadIdx.x == 0) {
+    s_next = atomicAdd(&ctl[0], 1);
+    mbar_init(&s_bars[0], 1);
+    mbar_init(&s_bars[1], 1);
+    fence_mbar_init();
+  }
   for (;;) {
     if (threadIdx.x == 0) {
       s_unit = s_next;
@@ -155,6 +192,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1) k_batch(const
     __syncthreads();
     if (s_abort) break;
     const Desc &d = sd;
+    bool tma_failed = false;
     switch (u.y) {
       case K_FACTOR:
         unit_factor<T>(d, u.z * kFactorPerUnit, kFactorPerUnit, blockDim.x);
@@ -173,6 +211,19 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1) k_batch(const
         unit_small<T>(d, sm);
         break;
       case K_COL: {
+        if constexpr (sizeof(T) == 4) {
+          if (d.flags & F_COL_TMA) {
+            const int cnt = d.cols_per_unit;
+            const int c0 = u.z * d.col_g * cnt;
+            const int c1 = min(d.M + 1, c0 + d.col_g * cnt);
+            const int r = col_tma_unit(d, c0, c1, cnt, sm, s_bars, tma_ph, &s_abort);
+            if (r < 0) {
+              if (threadIdx.x == 0) atomicCAS(&ctl[1], 0, -6 /* FS_ERR_TIMEOUT */);
+              tma_failed = true;
+            }
+            if (r != 0) break;
+          }
+        }
         const int groups = (d.M + 1 + d.cols_per_unit - 1) / d.cols_per_unit;
         for (int g = 0; g < d.col_g; ++g) {
           const int grp = u.z * d.col_g + g;
@@ -184,6 +235,15 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1) k_batch(const
       }
       case K_C2R: {
         const int tiles = (d.ny + d.rows_per_unit - 1) / d.rows_per_unit;
+        if constexpr (sizeof(T) == 4) {
+          if (d.flags & F_ROW_STAGED) {
+            const int t0 = u.z * d.row_g, t1 = min(tiles, t0 + d.row_g);
+            if (c2r_staged_unit(d, t0, t1, d.rows_per_unit, sm,
+                                reinterpret_cast<const cx<float> *>(u.w ? d.work_v : d.work_u),
+                                reinterpret_cast<float *>(u.w ? d.out_v : d.out_u)))
+              break;
+          }
+        }
         for (int g = 0; g < d.row_g; ++g) {
           const int tile = u.z * d.row_g + g;
           if (tile >= tiles) break;
@@ -195,6 +255,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1) k_batch(const
       default:
         break;
     }
+    if (tma_failed) break;  // uniform: every thread read the same abort flag
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();

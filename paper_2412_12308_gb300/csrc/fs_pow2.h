@@ -16,6 +16,8 @@ constexpr bool p2_col_ok(int L) { return L >= 128 && L <= 8192 && (L & (L - 1)) 
 constexpr int p2_row_cnt(int M) {
   return (M / 16) >= 256 ? 2 : ((M / 16) * 16 <= 512 ? 16 : 512 / (M / 16));
 }
+// rows per tile of a 256-thread batch CTA (p2_row_cnt(M) where it fits)
+constexpr int p2_row_cnt_256(int M) { return (M / 16) * p2_row_cnt(M) <= 256 ? p2_row_cnt(M) : 256 / (M / 16); }
 constexpr bool p2_row_ok(int M) { return M >= 128 && M <= 4096 && (M & (M - 1)) == 0; }
 // Complex (C2C) rows of length N: up to 16 rows and 512 threads per CTA.
 constexpr int p2_c2c_cnt(int N) { return (N / 16) * 16 <= 512 ? 16 : 512 / (N / 16); }
@@ -34,6 +36,10 @@ __device__ bool p2_unit_col1(const Desc &d, int unit, int cnt, cx<float> *sm, cx
 // columns of an advance with a constant source, one or two fields
 __device__ bool p2_unit_cols(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu, cx<float> *wv,
                              bool sh);
+
+// Batch column units staged by bulk copies (F_COL_TMA, fs_col_tma.cuh):
+// shared memory of those units: two padded group buffers
+size_t p2_col1_tma_unit_smem(int L, int cnt);
 
 // Kernel lookup (nullptr when not specialised).
 PassKernel p2_r2c_f32(int M);

@@ -1,4 +1,5 @@
 // FP32 pass kernels specialised for power-of-two lengths (see fs_pow2.h).
+#include "fs_col_tma.cuh"
 #include "fs_pow2.h"
 #include "fs_tma.cuh"
 #include "fs_units.cuh"
@@ -91,90 +92,6 @@ __global__ void __launch_bounds__(C2CK<N>::THREADS, min_blocks<C2CK<N>::THREADS>
                                             reinterpret_cast<cx<float> *>(d.out_u), true);
 }
 
-// ---------------------------------------------------------------- TMA column pass
-// Persistent CTAs walk column groups a = blockIdx.x*CC, += gridDim.x*CC.  The
-// CC columns of a group are one contiguous run of the x-frequency-major
-// spectrum, so a single bulk copy (cp.async.bulk, completion on an mbarrier)
-// stages the NEXT group into shared memory while the current group is
-// transformed; the current buffer doubles as the FFT exchange area.  Single
-// field only (the two-field wave variants use k_col_p2).
-template <int L, int CC>
-__device__ __forceinline__ void col_tma_body(const Desc &d, cx<float> *buf0, cx<float> *buf1, uint64_t *bars,
-                                             int *s_abort) {
-  constexpr int E = 16, Tseg = L / E;
-  const int tid = threadIdx.x;
-  const int rho = tid / Tseg, t = tid - rho * Tseg;
-  const int ncols = d.M + 1;
-  const bool adv = (d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV);
-  const cx<float> *src = reinterpret_cast<const cx<float> *>(adv ? d.st_u : d.work_u);
-  cx<float> *dst = reinterpret_cast<cx<float> *>(d.work_u);
-  const cx<float> *tw = reinterpret_cast<const cx<float> *>(d.tw_y);
-  const int g0 = blockIdx.x * CC, gstride = gridDim.x * CC;
-  auto issue = [&](cx<float> *b, uint64_t *bar, int g) {
-    const int nc = min(CC, ncols - g);
-    const uint32_t bytes = (uint32_t)(nc * L * sizeof(cx<float>));
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(b, src + (size_t)g * L, bytes, bar);
-  };
-  if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_mbar_init();
-    *s_abort = 0;
-    if (g0 < ncols) issue(buf0, &bars[0], g0);
-  }
-  __syncthreads();
-  int i = 0;
-  for (int g = g0; g < ncols; g += gstride, ++i) {
-    cx<float> *cur = (i & 1) ? buf1 : buf0;
-    cx<float> *nxt = (i & 1) ? buf0 : buf1;
-    if (tid == 0 && g + gstride < ncols) {
-      fence_proxy_async_smem();
-      issue(nxt, &bars[(i + 1) & 1], g + gstride);
-    }
-    // every thread observes the copy's completion itself (bounded)
-    if (!mbar_wait_bounded(&bars[i & 1], (uint32_t)((i >> 1) & 1), kTmaWaitNs)) {
-      atomicExch(&g_fs_dev_error, FS_DEV_ERR_TMA_TIMEOUT);
-      *s_abort = 1;
-    }
-    __syncthreads();
-    if (*s_abort) {
-      // let the copy still in flight land before the CTA exits
-      if (tid == 0 && g + gstride < ncols)
-        mbar_wait_bounded(&bars[(i + 1) & 1], (uint32_t)(((i + 1) >> 1) & 1), kTmaWaitNs);
-      break;
-    }
-    const int a = g + rho;
-    const bool active = a < ncols;
-    cx<float> u[E];
-    if (active) {
-#pragma unroll
-      for (int s = 0; s < E; ++s) u[s] = cur[rho * L + t + Tseg * s];
-    } else {
-#pragma unroll
-      for (int s = 0; s < E; ++s) u[s] = zero_cx<float>();
-    }
-    const XLayout lay{rho * L, 1};
-    if (!adv) fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
-    if (!adv && d.st_out_u && active) {  // keep the forward spectrum
-      cx<float> *ou = reinterpret_cast<cx<float> *>(d.st_out_u) + (size_t)a * L;
-#pragma unroll
-      for (int s = 0; s < E; ++s) ou[t + Tseg * s] = u[s];
-    }
-    if (d.op != OP_FORWARD) {
-      if (active) col_op_single<float, E>(d, op_ctx<float>(d, a), t, Tseg, u);
-      __syncthreads();
-      fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
-      if (active) {
-        cx<float> *o = dst + (size_t)a * L;
-#pragma unroll
-        for (int s = 0; s < E; ++s) o[t + Tseg * s] = conj(u[s]);
-      }
-    }
-    __syncthreads();
-  }
-}
-
 template <int L>
 struct ColT {
   static constexpr int CC = p2_col_cnt(L);
@@ -188,7 +105,15 @@ __global__ void __launch_bounds__(ColT<L>::THREADS, ColT<L>::THREADS >= 512 ? 1 
   __shared__ uint64_t bars[2];
   __shared__ int s_abort;
   cx<float> *b0 = reinterpret_cast<cx<float> *>(fs_smem);
-  col_tma_body<L, ColT<L>::CC>(d, b0, b0 + ColT<L>::PLEN, bars, &s_abort);
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  uint32_t ph = 0;
+  constexpr int CC = ColT<L>::CC;
+  col_tma_groups<L, CC>(d, blockIdx.x * CC, gridDim.x * CC, d.M + 1, CC, b0, b0 + ColT<L>::PLEN, bars, ph,
+                        &s_abort);
 }
 
 #define FS_P2_ROWS(X) X(128) X(256) X(512) X(1024) X(2048) X(4096)
@@ -206,7 +131,6 @@ __device__ __noinline__ void p2_c2r_unit(const Desc &d, int unit, cx<float> *sm,
                                          bool sh) {
   unit_row_c2r_t<float, 16, M, CC>(d, unit, CC, sm, spec, out, sh);
 }
-constexpr int p2_row_cnt_256(int M) { return (M / 16) * p2_row_cnt(M) <= 256 ? p2_row_cnt(M) : 256 / (M / 16); }
 template <int L>
 __device__ __noinline__ void p2_col1_unit(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu,
                                           cx<float> *wv, bool sh) {
@@ -267,6 +191,10 @@ __device__ bool p2_unit_col1(const Desc &d, int unit, int cnt, cx<float> *sm, cx
     default:
       return false;
   }
+}
+
+size_t p2_col1_tma_unit_smem(int L, int cnt) {
+  return 2 * (size_t)((padded_len(cnt * L) + 1) & ~1) * sizeof(cx<float>);
 }
 
 PassKernel p2_r2c_f32(int M) {

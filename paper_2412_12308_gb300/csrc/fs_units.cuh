@@ -180,33 +180,17 @@ __device__ __forceinline__ void unit_row_c2c_t(const Desc &d, int unit, int cnt_
 // the inverse length-M transform of F + iG gives x_{2m} + i x_{2m+1}.
 // The imaginary parts of X_0 and X_M are ignored (they are zero for a real
 // result).  No scaling here: 1/(nx ny) is folded into the spectral multiplier.
-template <typename T, int E, int MC = 0, int CC = 0>
-__device__ __forceinline__ void unit_row_c2r_t(const Desc &d, int unit, int cnt_rt, cx<T> *sm,
-                                               const cx<T> *spec, T *out, bool sh) {
+//
+// c2r_tile_finish is the part after the loads: v[s] holds X_k, k = t + Tseg*s,
+// of the thread's row, xM holds X_M (thread t == 0), and xs(j) returns X_j of
+// the thread's row from shared memory (wherever the caller staged the tile).
+template <typename T, int E, int MC, int CC, typename XS>
+__device__ __forceinline__ void c2r_tile_finish(const Desc &d, int unit, int cnt, int t, int rho, bool active,
+                                                cx<T> (&v)[E], cx<T> xM, XS xs, cx<T> *sm, T *out) {
   const int M = MC ? MC : d.M, ny = d.ny, Tseg = M / E;
-  const int cnt = CC ? CC : cnt_rt;
   const int tid = threadIdx.x;
-  const int t = tid / cnt, rho = tid - t * cnt;
-  const int y = unit * cnt + rho;
-  const bool active = (t < Tseg) && (y < ny);
   const XLayout lay{rho, cnt};
   const cx<T> *tw = reinterpret_cast<const cx<T> *>(d.tw_x);
-  cx<T> v[E];
-  cx<T> xM = zero_cx<T>();
-  if (active) {
-#pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = ldc(spec + (size_t)(t + Tseg * s) * ny + y, sh);
-    if (t == 0) xM = ldc(spec + (size_t)M * ny + y, sh);
-  } else {
-#pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();
-  }
-  __syncthreads();
-  if (active) {
-#pragma unroll
-    for (int s = 0; s < E; ++s) sm[padi(rho + (t + Tseg * s) * cnt)] = v[s];
-  }
-  __syncthreads();
   if (active) {
 #pragma unroll
     for (int s = 0; s < E; ++s) {
@@ -216,7 +200,7 @@ __device__ __forceinline__ void unit_row_c2r_t(const Desc &d, int unit, int cnt_
         xk = mk<T>(xk.x, T(0));
         xm = mk<T>(xM.x, T(0));
       } else {
-        xm = conj(sm[padi(rho + (M - k) * cnt)]);
+        xm = conj(xs(M - k));
       }
       const cx<T> f = xk + xm;
       const cx<T> g = cmul(xk - xm, conj(tw[k]));
@@ -243,6 +227,35 @@ __device__ __forceinline__ void unit_row_c2r_t(const Desc &d, int unit, int cnt_
     }
   }
   __syncthreads();
+}
+
+template <typename T, int E, int MC = 0, int CC = 0>
+__device__ __forceinline__ void unit_row_c2r_t(const Desc &d, int unit, int cnt_rt, cx<T> *sm,
+                                               const cx<T> *spec, T *out, bool sh) {
+  const int M = MC ? MC : d.M, ny = d.ny, Tseg = M / E;
+  const int cnt = CC ? CC : cnt_rt;
+  const int tid = threadIdx.x;
+  const int t = tid / cnt, rho = tid - t * cnt;
+  const int y = unit * cnt + rho;
+  const bool active = (t < Tseg) && (y < ny);
+  cx<T> v[E];
+  cx<T> xM = zero_cx<T>();
+  if (active) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = ldc(spec + (size_t)(t + Tseg * s) * ny + y, sh);
+    if (t == 0) xM = ldc(spec + (size_t)M * ny + y, sh);
+  } else {
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) sm[padi(rho + (t + Tseg * s) * cnt)] = v[s];
+  }
+  __syncthreads();
+  c2r_tile_finish<T, E, MC, CC>(d, unit, cnt, t, rho, active, v, xM,
+                                [&](int j) { return sm[padi(rho + j * cnt)]; }, sm, out);
 }
 
 // ------------------------------------------------------------ column group

@@ -4,12 +4,15 @@ Checks: every problem of an uneven mixed batch matches the float64 oracle
 (rel-L2 <= 1e-5; normwise for strongly decayed diffusion outputs); a request's
 result is bit-identical alone and in a mix; batched results agree with the
 per-call entry points; a repeated batch shape replays its CUDA graph with the
-same results; and an injected dependency that never completes ends the
-launch through the bounded wait with FS_ERR_TIMEOUT, leaving the context
-usable.
+same results; staged column groups and C2R tiles (bulk / asynchronous
+copies into shared memory) give results bit-identical to the unstaged units;
+and an injected dependency that never completes ends the launch through the
+bounded wait with FS_ERR_TIMEOUT, leaving the context usable.
 """
 
 import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -226,3 +229,69 @@ def test_bounded_wait_expires_without_fault(gpu_lib, monkeypatch):
             assert check_vs_oracle(P, i, P.outputs[i].double().cpu().numpy()) <= 1e-5
     finally:
         P.close()
+
+
+# (nx, ny): power-of-two rows and columns (staged), a ragged last C2R tile
+# (ny = 40 with 16-row tiles), rows of 8192 (one-row tiles: unstaged),
+# non-power-of-two columns (unstaged columns, staged rows)
+STAGED_SHAPES = [(256, 40), (1024, 96), (2048, 256), (512, 512), (1024, 1024), (8192, 128)]
+
+
+def staged_case():
+    """One batch over STAGED_SHAPES: the three solves, diffusion and wave
+    advances from kept spectra (the wave also with v).  Returns the outputs
+    in request order."""
+    rng = np.random.default_rng(321)
+    plans, states, outs, reqs = [], [], [], []
+    try:
+        for nx, ny in STAGED_SHAPES:
+            plan = fsolve.fs_plan_create(nx, ny, 1.0, 1.3, F32)
+            plans.append(plan)
+            f = torch.tensor(rng.standard_normal((ny, nx)), dtype=torch.float32, device="cuda")
+            g = torch.tensor(rng.standard_normal((ny, nx)), dtype=torch.float32, device="cuda")
+            s1, s2 = fsolve.fs_state_create(plan, f), fsolve.fs_state_create(plan, f, g)
+            states += [s1, s2]
+
+            def out():
+                outs.append(torch.full((ny, nx), float("nan"), dtype=torch.float32, device="cuda"))
+                return outs[-1]
+            reqs.append(fsolve.fs_request(fsolve.FS_OP_POISSON, plan=plan, in_u=f, out_u=out()))
+            reqs.append(fsolve.fs_request(fsolve.FS_OP_DIFFUSION, plan=plan, in_u=f, out_u=out(), D=0.01, t=0.3))
+            reqs.append(fsolve.fs_request(fsolve.FS_OP_WAVE, plan=plan, in_u=f, out_u=out(), c=1.0, t=0.4))
+            reqs.append(fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, state=s1, out_u=out(), D=0.01, t=0.2))
+            reqs.append(fsolve.fs_request(fsolve.FS_OP_WAVE_ADVANCE, state=s1, out_u=out(), c=1.0, t=0.7))
+            u, v = out(), out()
+            reqs.append(fsolve.fs_request(fsolve.FS_OP_WAVE_ADVANCE, state=s2, out_u=u, out_v=v, c=1.0, t=0.7))
+        fsolve.fs_batch_wait(fsolve.fs_batch_submit(reqs), 30_000_000)
+        torch.cuda.synchronize()
+        return [o.cpu().numpy() for o in outs]
+    finally:
+        for st in states:
+            fsolve.fs_state_destroy(st)
+        for plan in plans:
+            fsolve.fs_plan_destroy(plan)
+
+
+_UNSTAGED = """
+import sys
+import numpy as np
+from tests.test_batch_gpu import staged_case
+np.savez(sys.argv[1], *staged_case())
+"""
+
+
+def test_staged_units_bit_identical_to_unstaged(gpu_lib, tmp_path, monkeypatch):
+    """Staging moves data only: the staged batch (this process) and the
+    unstaged one (a child process with FS_NO_TMA=1) agree bit for bit, and
+    every output is finite.  Problems run as units (no single-CTA path)."""
+    monkeypatch.setenv("FS_BATCH_SMALL_MAX", "0")
+    got = staged_case()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, FS_NO_TMA="1", FS_BATCH_SMALL_MAX="0")
+    path = tmp_path / "unstaged.npz"
+    subprocess.run([sys.executable, "-c", _UNSTAGED, str(path)], env=env, cwd=root, check=True, timeout=600)
+    ref = np.load(path)
+    assert len(ref.files) == len(got)
+    for i, o in enumerate(got):
+        assert np.isfinite(o).all(), i
+        assert np.array_equal(o, ref[f"arr_{i}"]), (i, STAGED_SHAPES[i // 7])
