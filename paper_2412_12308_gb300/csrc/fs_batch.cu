@@ -302,18 +302,25 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
       tiles += (d.ny + d.rows_per_unit - 1) / d.rows_per_unit;
       tiles += (d.M + 1 + d.cols_per_unit - 1) / d.cols_per_unit;
     }
-    // measured on GB300: 2-4 groups per unit beat 1 (per-unit overhead) and 8
-    // (too few units to balance); aim for ~24 units per SM
-    int G = (int)(tiles / (24LL * 152LL));
-    G = G < 1 ? 1 : (G > 4 ? 4 : G);
-    if (const char *v = getenv("FS_BATCH_GROUP")) G = atoi(v) > 0 ? atoi(v) : G;
+    // measured on GB300 with staged units (the first tile of a unit is loaded
+    // unhidden, the rest behind the previous tile's compute), 100 advances
+    // per batch: 3 per unit beat 4 at 256^2..1536^2 (512^2: 153 vs 161 us,
+    // 768^2: 898 vs 1005 us) and 1-2 (512^2: 0.207 ms at 1), 4 beat 3 from
+    // 1024^2 up (2048^2: 2073 vs 2179 us), 6-8 lose (too few units to
+    // balance); a batch with few tiles keeps one per unit so that they
+    // spread over the CTAs
+    int G = (int)(tiles / (4LL * 152LL));
+    G = G < 1 ? 1 : (G > 3 ? 3 : G);
+    const char *genv = getenv("FS_BATCH_GROUP");
     for (int k = 0; k < n; ++k) {
       Desc &d = bp->descs[k];
-      d.row_g = d.col_g = G;
+      int g = (G == 3 && (long long)d.nx * d.ny >= 1024LL * 1024LL) ? 4 : G;
+      if (genv && atoi(genv) > 0) g = atoi(genv);
+      d.row_g = d.col_g = g;
       const int rt = (d.ny + d.rows_per_unit - 1) / d.rows_per_unit;
       const int cg = (d.M + 1 + d.cols_per_unit - 1) / d.cols_per_unit;
-      d.n_row_units = (rt + G - 1) / G;
-      d.n_col_units = (cg + G - 1) / G;
+      d.n_row_units = (rt + g - 1) / g;
+      d.n_col_units = (cg + g - 1) / g;
     }
   }
   // chunks by intermediate bytes

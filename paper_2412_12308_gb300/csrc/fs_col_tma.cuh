@@ -87,7 +87,8 @@ __device__ __forceinline__ bool col_tma_groups(const Desc &d, int g_first, int g
     }
     if (d.op != OP_FORWARD) {
       if (active) col_op_single<float, E>(d, op_ctx<float>(d, a), t, Tseg, u);
-      __syncthreads();
+      // no barrier here: the transform's first exchange store into `cur`
+      // comes after its own barrier, which every read of `cur` above precedes
       fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
       if (active) {
         cx<float> *o = dst + (size_t)a * L;
