@@ -41,6 +41,10 @@ def _jobs():
                     # the units are called from kernels launched with <= 512 threads
                     out.append((src, [f"-DFS_T={t}", f"-DFS_E={e}", "-maxrregcount=128"],
                                 f"units_{t}_e{e}.o"))
+        elif name == "fs_mixed_f32.cu":
+            # one object per family (3 x 2^k, 5 x 2^k); units called from <= 512-thread kernels
+            for odd in (3, 5):
+                out.append((src, [f"-DFS_MX_ODD={odd}", "-maxrregcount=128"], f"mixed_f32_{odd}.o"))
         elif name in ("fs_pow2_f32.cu", "fs_pow2_src_f32.cu"):
             # its device units are called from kernels launched with <= 512 threads
             out.append((src, ["-maxrregcount=128"], name + ".o"))

@@ -317,13 +317,17 @@ __device__ __forceinline__ void fft_run(cx<T> (&v)[E], cx<T> *sm, XLayout lay, b
 }
 
 // ------------------------------------------------------------ compile-time engine
-// For power-of-two lengths L and tiles E the stage radices, the running
-// product Ns and every index stride are compile-time constants, so the shared
-// memory addresses reduce to a per-thread base plus immediate offsets.  Same
-// stage sequence and arithmetic as fft_run (largest radix dividing E first).
+// For lengths L = m 2^k (m in {1, 3, 5}) and tiles E = m 2^j the stage
+// radices, the running product Ns and every index stride are compile-time
+// constants, so the shared memory addresses reduce to a per-thread base plus
+// immediate offsets.  Same stage sequence and arithmetic as fft_run with the
+// plan of radix_plan: power-of-two radices, largest dividing E first, then
+// the odd radix m as the last stage.  Ns = product of the earlier radices and
+// Tseg = L/E are therefore powers of two at every stage.
 namespace ct {
 constexpr int first_radix(int E) { return E % 16 == 0 ? 16 : (E % 8 == 0 ? 8 : (E % 4 == 0 ? 4 : 2)); }
 constexpr int pick(int rem, int E) {
+  if (rem == 3 || rem == 5) return rem;  // the odd stage, last
   int r = first_radix(E);
   while (rem % r) r >>= 1;
   return r;
@@ -348,6 +352,13 @@ constexpr int ns(int L, int E, int st) {
   return p;
 }
 constexpr bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+// lengths and tiles the engine takes: odd part of L in {1, 3, 5}, E carrying
+// the same odd part, L/E a power of two
+constexpr int odd_part(int x) { return x % 2 == 0 ? odd_part(x / 2) : x; }
+constexpr bool ok(int L, int E) {
+  return L > 0 && E > 0 && L % E == 0 && (odd_part(L) == 1 || odd_part(L) == 3 || odd_part(L) == 5) &&
+         odd_part(E) == odd_part(L) && is_pow2(L / E);
+}
 }  // namespace ct
 
 template <typename T, int E, int L, int SIDX, int TWMUL, int ST>
@@ -360,6 +371,7 @@ __device__ __forceinline__ void fft_ct_from(cx<T> (&v)[E], cx<T> *sm, int base, 
     constexpr int Tseg = L / E;
     constexpr int Q = E / R;
     static_assert(E % R == 0, "radix must divide the tile");
+    static_assert(ct::is_pow2(NS) && ct::is_pow2(Tseg), "odd stage last: Ns and Tseg are powers of two");
     if constexpr (ST > 0) {
       if (active) {
         const int pb = base + t * SIDX;
@@ -430,7 +442,7 @@ __device__ __forceinline__ void fft_any(cx<T> (&v)[E], cx<T> *sm, XLayout lay, b
                                         int Tseg, int L, const RadixPlan &rp,
                                         const cx<T> *__restrict__ tw) {
   if constexpr (LC > 0) {
-    static_assert(SIDX > 0 && ct::is_pow2(LC), "compile-time engine: pow2 length, fixed stride");
+    static_assert(SIDX > 0 && ct::ok(LC, E), "compile-time engine: length m 2^k, tile m 2^j, fixed stride");
     fft_ct_from<T, E, LC, SIDX, TWMUL, 0>(v, sm, lay.base, active, t, tw);
   } else {
     fft_run<T, E>(v, sm, lay, active, t, Tseg, L, rp, tw, TWMUL);

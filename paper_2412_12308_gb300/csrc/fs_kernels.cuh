@@ -5,6 +5,7 @@
 #include <atomic>
 
 #include "fs_col_tma.cuh"
+#include "fs_mixed.h"
 #include "fs_pow2.h"
 #include "fs_row_async.cuh"
 #include "fs_tma.cuh"
@@ -300,6 +301,12 @@ struct Launch {
       return nullptr;
     return c2r ? p2_c2r_f32(d.M) : p2_r2c_f32(d.M);
   }
+  // FP32 3 x 2^k / 5 x 2^k kernels with compile-time lengths, same condition
+  static PassKernel mx_row(const Desc &d, bool c2r) {
+    if (sizeof(T) != 4 || !mx_row_ok(d.M) || d.rp_row.e != mx_e(d.M) || d.rows_per_unit != mx_row_cnt(d.M))
+      return nullptr;
+    return c2r ? mx_c2r_f32(d.M) : mx_r2c_f32(d.M);
+  }
   static PassKernel p2_col(const Desc &d) {
     if (sizeof(T) != 4 || d.rp_col.e != 16 || !p2_col_ok(d.ny) || d.cols_per_unit != p2_col_cnt(d.ny))
       return nullptr;
@@ -319,6 +326,7 @@ struct Launch {
   // forward pass over the real field(s): fields = 1 or 2
   static cudaError_t rows(const Desc &d, int fields, cudaStream_t s) {
     PassKernel k = p2_row(d, false);
+    if (!k) k = mx_row(d, false);
     if (!k) k = pass_kernels<T>(d.rp_row.e).r2c;
     return launch(k, d.n_row_units * fields, row_threads(d), row_smem(d), d, s, PC_R2C);
   }
@@ -358,6 +366,8 @@ struct Launch {
       return cudaGetLastError();
     }
     PassKernel k = p2_col(d);
+    if (!k && sizeof(T) == 4 && !col_two_fields(d) && mx_col_ok(d.ny) && d.rp_col.e == mx_e(d.ny))
+      k = mx_col1_f32(d.ny);
     if (!k) {
       const PassKernels pk = pass_kernels<T>(d.rp_col.e);
       k = col_two_fields(d) ? pk.col2 : pk.col1;
@@ -366,6 +376,7 @@ struct Launch {
   }
   static cudaError_t c2r(const Desc &d, int fields, cudaStream_t s) {
     PassKernel k = p2_row(d, true);
+    if (!k) k = mx_row(d, true);
     if (!k) k = pass_kernels<T>(d.rp_row.e).c2r;
     return launch(k, d.n_row_units * fields, row_threads(d), row_smem(d), d, s, PC_C2R);
   }

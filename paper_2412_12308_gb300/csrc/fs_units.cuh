@@ -16,6 +16,7 @@
 // and read runs of `rows_per_unit` consecutive y values per frequency.
 #pragma once
 #include <type_traits>
+#include "fs_mixed.h"
 #include "fs_ops.cuh"
 #include "fs_pow2.h"
 
@@ -676,6 +677,29 @@ __device__ __forceinline__ bool pow2_cols(const Desc &, int, int, cx<double> *, 
   return false;
 }
 
+// Compile-time 3 x 2^k / 5 x 2^k units (FP32 only; fs_mixed_f32.cu).
+__device__ __forceinline__ bool mixed_r2c(const Desc &d, int unit, int cnt, cx<float> *sm, const float *in,
+                                          cx<float> *spec) {
+  return mx_unit_r2c(d, unit, cnt, sm, in, spec);
+}
+__device__ __forceinline__ bool mixed_r2c(const Desc &, int, int, cx<double> *, const double *, cx<double> *) {
+  return false;
+}
+__device__ __forceinline__ bool mixed_c2r(const Desc &d, int unit, int cnt, cx<float> *sm, const cx<float> *spec,
+                                          float *out, bool sh) {
+  return mx_unit_c2r(d, unit, cnt, sm, spec, out, sh);
+}
+__device__ __forceinline__ bool mixed_c2r(const Desc &, int, int, cx<double> *, const cx<double> *, double *, bool) {
+  return false;
+}
+__device__ __forceinline__ bool mixed_col1(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu,
+                                           cx<float> *wv, bool sh) {
+  return mx_unit_col1(d, unit, cnt, sm, wu, wv, sh);
+}
+__device__ __forceinline__ bool mixed_col1(const Desc &, int, int, cx<double> *, cx<double> *, cx<double> *, bool) {
+  return false;
+}
+
 template <typename T>
 struct Units;
 #define FS_UNITS_SPEC(T)                                                                        \
@@ -684,11 +708,13 @@ struct Units;
     static __device__ __forceinline__ void r2c(const Desc &d, int unit, int cnt, cx<T> *sm,     \
                                                const T *in, cx<T> *spec) {                      \
       if (pow2_r2c(d, unit, cnt, sm, in, spec)) return;                                         \
+      if (mixed_r2c(d, unit, cnt, sm, in, spec)) return;                                        \
       FS_E_SWITCH_##T(d.rp_row.e, unit_row_r2c, d, unit, cnt, sm, in, spec)                      \
     }                                                                                           \
     static __device__ __forceinline__ void c2r(const Desc &d, int unit, int cnt, cx<T> *sm,     \
                                                const cx<T> *spec, T *out, bool sh) {            \
       if (pow2_c2r(d, unit, cnt, sm, spec, out, sh)) return;                                    \
+      if (mixed_c2r(d, unit, cnt, sm, spec, out, sh)) return;                                   \
       FS_E_SWITCH_##T(d.rp_row.e, unit_row_c2r, d, unit, cnt, sm, spec, out, sh)                 \
     }                                                                                           \
     static __device__ __forceinline__ void col(const Desc &d, int unit, int cnt, cx<T> *sm,     \
@@ -700,6 +726,7 @@ struct Units;
         FS_E_SWITCH_##T(d.rp_col.e, unit_col2, d, unit, cnt, sm, wu, wv, sh)                    \
       } else {                                                                                  \
         if (pow2_col1(d, unit, cnt, sm, wu, wv, sh)) return;                                    \
+        if (mixed_col1(d, unit, cnt, sm, wu, wv, sh)) return;                                   \
         FS_E_SWITCH_##T(d.rp_col.e, unit_col, d, unit, cnt, sm, wu, wv, sh)                     \
       }                                                                                         \
     }                                                                                           \

@@ -15,7 +15,7 @@ import torch
 
 import oracle
 from oracle import closed_forms as cf
-from paper_2412_12308_gb300 import workloads as wl
+from paper_2412_12308_gb300 import fsolve, workloads as wl
 
 pytestmark = pytest.mark.gpu
 
@@ -201,27 +201,40 @@ def test_rejections_on_device(gpu_lib):
             gpu_lib.fs_poisson_solve(p.h, None, x)
 
 
-@pytest.mark.parametrize("n", [2048, 4096, 8192])
-def test_large_grids_sampled(gpu_lib, n):
-    """Large FP32 grids: mode-sum sources have exact closed forms on every
-    grid point (O(modes * N^2)), so the whole output is checked."""
-    rng = np.random.default_rng(n)
+@pytest.mark.parametrize("nx,ny", [(2048, 2048), (4096, 4096), (8192, 8192), (1536, 1536), (2560, 2560),
+                                   (3072, 1280), (6144, 640), (5120, 384), (1280, 3072)])
+def test_large_grids_sampled(gpu_lib, nx, ny):
+    """Large FP32 grids (powers of two, 3 x 2^k and 5 x 2^k lengths, square
+    and rectangular): mode-sum sources have exact closed forms on every grid
+    point (O(modes * N^2)), so the whole output is checked, through the
+    per-call entry points and through one batch."""
+    rng = np.random.default_rng(nx + 7 * ny)
     modes = wl.draw_modes(rng, 8, 40)
-    f = wl.mode_sum(modes, n, n, 1.0, 1.0)
-    with Plan(gpu_lib, n, n, 1.0, 1.0, 0) as p:
+    f = wl.mode_sum(modes, nx, ny, 1.0, 1.0)
+    with Plan(gpu_lib, nx, ny, 1.0, 1.0, 0) as p:
         fd = p.dev(f)
         ud = torch.empty_like(fd)
         gpu_lib.fs_poisson_solve(p.h, fd, ud)
-        assert rel(host(ud), cf.poisson_modes(modes, n, n, 1.0, 1.0)) <= 1e-5
+        u_p = cf.poisson_modes(modes, nx, ny, 1.0, 1.0)
+        assert rel(host(ud), u_p) <= 1e-5
         # D t chosen so the output keeps most of the input energy (a heavily
         # decayed output is compared normwise in test_diffusion_heavy_decay)
         gpu_lib.fs_diffusion_solve(p.h, fd, 1e-5, 0.5, ud)
-        assert rel(host(ud), cf.diffusion_modes(modes, 1e-5, 0.5, n, n, 1.0, 1.0)) <= 1e-5
+        u_d = cf.diffusion_modes(modes, 1e-5, 0.5, nx, ny, 1.0, 1.0)
+        assert rel(host(ud), u_d) <= 1e-5
         st = gpu_lib.fs_state_create(p.h, fd)
         try:
             for t in (0.3, 1.0, 1.9):
                 gpu_lib.fs_wave_advance(st, 1.0, t, ud)
-                assert rel(host(ud), cf.wave_modes(modes, 1.0, t, n, n, 1.0, 1.0)) <= 1e-5
+                assert rel(host(ud), cf.wave_modes(modes, 1.0, t, nx, ny, 1.0, 1.0)) <= 1e-5
+            outs = [torch.empty_like(fd) for _ in range(3)]
+            reqs = [fsolve.fs_request(fsolve.FS_OP_POISSON, plan=p.h, in_u=fd, out_u=outs[0]),
+                    fsolve.fs_request(fsolve.FS_OP_DIFFUSION, plan=p.h, in_u=fd, out_u=outs[1], D=1e-5, t=0.5),
+                    fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, state=st, out_u=outs[2], D=1e-5, t=0.5)]
+            fsolve.fs_batch_wait(fsolve.fs_batch_submit(reqs), 60_000_000)
+            assert rel(host(outs[0]), u_p) <= 1e-5
+            assert rel(host(outs[1]), u_d) <= 1e-5
+            assert rel(host(outs[2]), u_d) <= 1e-5
         finally:
             gpu_lib.fs_state_destroy(st)
 
