@@ -210,8 +210,8 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 # of this workload from one ncu capture (profiles/k_batch_diffusion_1024.md),
 # valid only for the CUDA sources it was taken on: any change to them makes
 # the reported traffic null until a new capture.
-TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 244096512 + 794661376,
-                   "sources_sha256": "078c3307172715579b4d98ffab783843557bc90d8f375ac2b19fa887ea841759"}
+TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 166974976 + 790309376,
+                   "sources_sha256": "73b1992f4fecdf5e8f1bb2598c7ca743e496ef0b3c16243bb995f944476ffcea"}
 
 
 def _csrc_digest():
