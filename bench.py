@@ -210,8 +210,8 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 # of this workload from one ncu capture (profiles/k_batch_diffusion_1024.md),
 # valid only for the CUDA sources it was taken on: any change to them makes
 # the reported traffic null until a new capture.
-TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 166974976 + 790309376,
-                   "sources_sha256": "73b1992f4fecdf5e8f1bb2598c7ca743e496ef0b3c16243bb995f944476ffcea"}
+TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 166362624 + 784208128,
+                   "sources_sha256": "18c12b3840511ad173a9e62a49851e1eafb8e97257d7c434541326e49d1236a4"}
 
 
 def _csrc_digest():

@@ -236,24 +236,34 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
   // CTA size: 256 threads (two CTAs per SM) when every problem run as units
   // has row and column transforms of at most 256 threads and none is a
   // single-CTA small problem (its whole solve would run on half the threads),
-  // else 512.  Measured on GB300: 100 advances of 1024^2 +9 %, a 512-problem
-  // mix with small problems -18 % at 256.  Tile shapes follow; a row's or
-  // column's arithmetic does not depend on how many share a CTA.
+  // else 512; 128 threads (four CTAs per SM: a block barrier holds 4 warps,
+  // not 8) when, in addition, every problem is an FP32 power-of-two grid of
+  // at least 512^2 whose transforms fit 128 threads (the staged compile-time
+  // units have tiles of that height; smaller grids lose to the per-unit
+  // overhead).  Measured on GB300, 100 advances per batch: 256 vs 512 at
+  // 1024^2 +9 %, a 512-problem mix with small problems -18 % at 256; 128 vs
+  // 256: 1024^2 504 -> 477 us, 512^2 149 -> 140 us, 2048^2 2006 -> 1950 us,
+  // 256^2 60 -> 63 us.  Tile shapes follow; a row's or column's arithmetic
+  // does not depend on how many share a CTA.
   {
     int need = 1;
+    bool p2_large = true;
     for (int k = 0; k < n; ++k) {
       if (bp->direct[k]) continue;
       const Desc &d = bp->descs[k];
       need = std::max(need, std::max(d.M / d.rp_row.e, d.ny / d.rp_col.e));
       if (d.small) need = kMaxThreads;
+      p2_large = p2_large && bp->dtype == FS_F32 && d.rp_row.e == 16 && d.rp_col.e == 16 && p2_row_ok(d.M) &&
+                 p2_col_ok(d.ny) && (long long)d.nx * d.ny >= 512LL * 512LL;
     }
-    const int bt = need <= 256 ? 256 : kMaxThreads;
+    const int bt = (need <= 128 && p2_large) ? 128 : (need <= 256 ? 256 : kMaxThreads);
     if (const char *v = getenv("FS_BATCH_THREADS")) {
       int maxe = 1;  // the override may force 256 when every transform fits
       for (int k = 0; k < n; ++k)
         if (!bp->direct[k])
           maxe = std::max(maxe, std::max(bp->descs[k].M / bp->descs[k].rp_row.e, bp->descs[k].ny / bp->descs[k].rp_col.e));
-      if (atoi(v) == 512 || (atoi(v) == 256 && maxe <= 256)) bp->threads = atoi(v);
+      if (atoi(v) == 512 || (atoi(v) == 256 && maxe <= 256) || (atoi(v) == 128 && maxe <= 128))
+        bp->threads = atoi(v);
       else bp->threads = bt;
     } else {
       bp->threads = bt;
@@ -281,7 +291,7 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
       // staged into shared memory by asynchronous copies while the previous
       // one computes
       if (bp->dtype == FS_F32 && !d.small && d.rp_row.e == 16 && p2_row_ok(d.M) && rr % 2 == 0 &&
-          (rr == p2_row_cnt(d.M) || rr == p2_row_cnt_256(d.M)) && tma_enabled())
+          (rr == p2_row_cnt(d.M) || rr == p2_row_cnt_256(d.M) || rr == p2_row_cnt_128(d.M)) && tma_enabled())
         d.flags |= F_ROW_STAGED;
       d.n_col_units = (d.M + 1 + cc - 1) / cc;
       if (d.small) {
@@ -562,7 +572,7 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
   e = occupancy(threads);
   // 256-thread CTAs only pay when two fit on an SM (a resident small problem's
   // half spectrum can take most of the shared memory); the tiles also fit 512
-  if (e == cudaSuccess && threads == 256 && per_sm < 2) {
+  if (e == cudaSuccess && threads <= 256 && per_sm < 2) {
     threads = kMaxThreads;
     e = occupancy(threads);
   }

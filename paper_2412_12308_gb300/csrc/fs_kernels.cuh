@@ -112,7 +112,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // one unit's barrier waits overlap the other's work); the batch plan picks 256
 // when every problem's transforms fit and shapes its tiles accordingly.
 template <typename T, int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1) k_batch(const Desc *__restrict__ descs,
+__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : (THREADS == 256 ? 2 : 1)) k_batch(const Desc *__restrict__ descs,
                                                        const int4 *__restrict__ units, int n_units,
                                                        int *ctl, int *done,
                                                        unsigned long long wait_ns) {
@@ -397,7 +397,7 @@ struct Launch {
   }
   typedef void (*BatchKernel)(const Desc *, const int4 *, int, int *, int *, unsigned long long);
   static BatchKernel batch_kernel(int threads) {
-    return threads == 256 ? k_batch<T, 256> : k_batch<T, kMaxThreads>;
+    return threads == 128 ? k_batch<T, 128> : (threads == 256 ? k_batch<T, 256> : k_batch<T, kMaxThreads>);
   }
   static cudaError_t batch(const Desc *descs, const int4 *units, int n_units, int *ctl, int *done,
                            int grid, int threads, size_t smem, unsigned long long wait_ns, cudaStream_t s) {

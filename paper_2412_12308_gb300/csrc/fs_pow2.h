@@ -18,6 +18,10 @@ constexpr int p2_row_cnt(int M) {
 }
 // rows per tile of a 256-thread batch CTA (p2_row_cnt(M) where it fits)
 constexpr int p2_row_cnt_256(int M) { return (M / 16) * p2_row_cnt(M) <= 256 ? p2_row_cnt(M) : 256 / (M / 16); }
+// and of a 128-thread batch CTA (0 when a row needs more threads)
+constexpr int p2_row_cnt_128(int M) {
+  return (M / 16) > 128 ? 0 : ((M / 16) * p2_row_cnt_256(M) <= 128 ? p2_row_cnt_256(M) : 128 / (M / 16));
+}
 constexpr bool p2_row_ok(int M) { return M >= 128 && M <= 4096 && (M & (M - 1)) == 0; }
 // Complex (C2C) rows of length N: up to 16 rows and 512 threads per CTA.
 constexpr int p2_c2c_cnt(int N) { return (N / 16) * 16 <= 512 ? 16 : 512 / (N / 16); }

@@ -137,20 +137,41 @@ __device__ __noinline__ void p2_col1_unit(const Desc &d, int unit, int cnt, cx<f
   unit_col_t<float, 16, false, L, 0>(d, unit, cnt, sm, wu, wv, sh);
 }
 
+// a row unit of tile height CC when the runtime count is CC (CC = 0: none)
+template <int M, int CC>
+__device__ __forceinline__ bool p2_r2c_try(const Desc &d, int unit, int cnt, cx<float> *sm, const float *in,
+                                           cx<float> *spec) {
+  if constexpr (CC > 0) {
+    if (cnt == CC) {
+      p2_r2c_unit<M, CC>(d, unit, sm, in, spec);
+      return true;
+    }
+  }
+  return false;
+}
+template <int M, int CC>
+__device__ __forceinline__ bool p2_c2r_try(const Desc &d, int unit, int cnt, cx<float> *sm, const cx<float> *spec,
+                                           float *out, bool sh) {
+  if constexpr (CC > 0) {
+    if (cnt == CC) {
+      p2_c2r_unit<M, CC>(d, unit, sm, spec, out, sh);
+      return true;
+    }
+  }
+  return false;
+}
+
+// tile heights: standalone kernels, 256-thread and 128-thread batch CTAs
 __device__ bool p2_unit_r2c(const Desc &d, int unit, int cnt, cx<float> *sm, const float *in, cx<float> *spec) {
   if (d.rp_row.e != 16) return false;
   switch (d.M) {
-#define C(m)                                                                   \
-  case m:                                                                      \
-    if (cnt == p2_row_cnt(m)) {                                                \
-      p2_r2c_unit<m>(d, unit, sm, in, spec);                                   \
-      return true;                                                             \
-    }                                                                          \
-    if (p2_row_cnt_256(m) != p2_row_cnt(m) && cnt == p2_row_cnt_256(m)) {      \
-      p2_r2c_unit<m, p2_row_cnt_256(m)>(d, unit, sm, in, spec);                \
-      return true;                                                             \
-    }                                                                          \
-    return false;
+#define C(m)                                                                                           \
+  case m:                                                                                              \
+    return p2_r2c_try<m, p2_row_cnt(m)>(d, unit, cnt, sm, in, spec) ||                                 \
+           p2_r2c_try<m, (p2_row_cnt_256(m) != p2_row_cnt(m) ? p2_row_cnt_256(m) : 0)>(d, unit, cnt, sm, in, \
+                                                                                      spec) ||         \
+           p2_r2c_try<m, (p2_row_cnt_128(m) != p2_row_cnt_256(m) ? p2_row_cnt_128(m) : 0)>(d, unit, cnt, sm,  \
+                                                                                         in, spec);
     FS_P2_ROWS(C)
 #undef C
     default:
@@ -161,17 +182,13 @@ __device__ bool p2_unit_c2r(const Desc &d, int unit, int cnt, cx<float> *sm, con
                             bool sh) {
   if (d.rp_row.e != 16) return false;
   switch (d.M) {
-#define C(m)                                                                   \
-  case m:                                                                      \
-    if (cnt == p2_row_cnt(m)) {                                                \
-      p2_c2r_unit<m>(d, unit, sm, spec, out, sh);                              \
-      return true;                                                             \
-    }                                                                          \
-    if (p2_row_cnt_256(m) != p2_row_cnt(m) && cnt == p2_row_cnt_256(m)) {      \
-      p2_c2r_unit<m, p2_row_cnt_256(m)>(d, unit, sm, spec, out, sh);           \
-      return true;                                                             \
-    }                                                                          \
-    return false;
+#define C(m)                                                                                              \
+  case m:                                                                                                 \
+    return p2_c2r_try<m, p2_row_cnt(m)>(d, unit, cnt, sm, spec, out, sh) ||                               \
+           p2_c2r_try<m, (p2_row_cnt_256(m) != p2_row_cnt(m) ? p2_row_cnt_256(m) : 0)>(d, unit, cnt, sm, spec, \
+                                                                                      out, sh) ||         \
+           p2_c2r_try<m, (p2_row_cnt_128(m) != p2_row_cnt_256(m) ? p2_row_cnt_128(m) : 0)>(d, unit, cnt, sm,   \
+                                                                                         spec, out, sh);
     FS_P2_ROWS(C)
 #undef C
     default:

@@ -78,7 +78,7 @@ __device__ __forceinline__ void c2r_staged_tiles(const Desc &d, int tile0, int t
 template <int M, int CC>
 __device__ __forceinline__ bool c2r_staged_try(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,
                                                const cx<float> *spec, float *out) {
-  if constexpr (CC % 2 == 0) {
+  if constexpr (CC > 0 && CC % 2 == 0) {
     if (cnt == CC) {
       c2r_staged_tiles<M, CC>(d, tile0, tile1, sm, spec, out);
       return true;
@@ -88,16 +88,18 @@ __device__ __forceinline__ bool c2r_staged_try(const Desc &d, int tile0, int til
 }
 
 // Dispatch on the row length and the tile height (the standalone kernels'
-// p2_row_cnt or the 256-thread batch's p2_row_cnt_256); false when neither
-// is compiled.
+// p2_row_cnt, the 256- or 128-thread batch's p2_row_cnt_256 / _128); false
+// when none is compiled.
 __device__ __forceinline__ bool c2r_staged_unit(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,
                                                 const cx<float> *spec, float *out) {
   switch (d.M) {
-#define FS_C2R_STAGED(m)                                                                   \
-  case m:                                                                                  \
+#define FS_C2R_STAGED(m)                                                                    \
+  case m:                                                                                   \
     if (c2r_staged_try<m, p2_row_cnt(m)>(d, tile0, tile1, cnt, sm, spec, out)) return true; \
-    if constexpr (p2_row_cnt_256(m) != p2_row_cnt(m))                                      \
-      return c2r_staged_try<m, p2_row_cnt_256(m)>(d, tile0, tile1, cnt, sm, spec, out);    \
+    if constexpr (p2_row_cnt_256(m) != p2_row_cnt(m))                                       \
+      if (c2r_staged_try<m, p2_row_cnt_256(m)>(d, tile0, tile1, cnt, sm, spec, out)) return true; \
+    if constexpr (p2_row_cnt_128(m) > 0 && p2_row_cnt_128(m) != p2_row_cnt_256(m))          \
+      return c2r_staged_try<m, p2_row_cnt_128(m)>(d, tile0, tile1, cnt, sm, spec, out);     \
     return false;
     FS_C2R_STAGED(128)
     FS_C2R_STAGED(256)
