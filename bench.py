@@ -210,8 +210,8 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 # of this workload from one ncu capture (profiles/k_batch_diffusion_1024.md),
 # valid only for the CUDA sources it was taken on: any change to them makes
 # the reported traffic null until a new capture.
-TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 166362624 + 784208128,
-                   "sources_sha256": "18c12b3840511ad173a9e62a49851e1eafb8e97257d7c434541326e49d1236a4"}
+TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 165655552 + 784329984,
+                   "sources_sha256": "aaa621d0c2bd51be45f63e4e096a682399e9ab06d9e17ec4d3f090c5497f29bb"}
 
 
 def _csrc_digest():
