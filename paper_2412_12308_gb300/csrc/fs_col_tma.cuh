@@ -46,6 +46,9 @@ __device__ __forceinline__ bool col_tma_groups(const Desc &d, int g_first, int g
   __syncthreads();
   if (tid == 0) {
     *s_abort = 0;
+    // a solve's work spectrum may come from other CTAs of this launch (seen
+    // through the batch's acquire): order it before the bulk copies read it
+    if (!adv) fence_proxy_async_global();
     if (g_first < g_end) issue(buf0, &bars[0], g_first);
   }
   __syncthreads();
