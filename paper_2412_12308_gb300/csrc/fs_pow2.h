@@ -41,8 +41,8 @@ __device__ bool p2_unit_col1(const Desc &d, int unit, int cnt, cx<float> *sm, cx
 __device__ bool p2_unit_cols(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu, cx<float> *wv,
                              bool sh);
 
-// Batch column units staged by bulk copies (F_COL_TMA, fs_col_tma.cuh):
-// shared memory of those units: two padded group buffers
+// Shared memory of a batch column unit staged by bulk copies (F_COL_TMA,
+// fs_col_tma.cuh): two padded buffers of cnt columns of length L.
 size_t p2_col1_tma_unit_smem(int L, int cnt);
 
 // Kernel lookup (nullptr when not specialised).
