@@ -67,8 +67,13 @@ __device__ __forceinline__ bool col_tma_groups(const Desc &d, int g_first, int g
     ph ^= 1u << k;
     __syncthreads();
     if (*s_abort) {
-      // let the copy still in flight land before the CTA leaves
-      if (tid == 0 && more) mbar_wait_bounded(&bars[k ^ 1], (ph >> (k ^ 1)) & 1u, kTmaWaitNs);
+      // let the copies still in flight land before the CTA leaves (bounded
+      // again): this group's, if it is the one that timed out (its phase
+      // parity is the one just flipped in ph), and the next group's
+      if (tid == 0) {
+        mbar_wait_bounded(&bars[k], ((ph >> k) & 1u) ^ 1u, kTmaWaitNs);
+        if (more) mbar_wait_bounded(&bars[k ^ 1], (ph >> (k ^ 1)) & 1u, kTmaWaitNs);
+      }
       return false;
     }
     const int a = g + rho;
