@@ -336,6 +336,12 @@ fs_status fs_batch_wait(uint64_t ticket, int timeout_us);
  *   max requests per batch.
  * fs_serve_enqueue: copy a request into the queue; *ticket_out names it.
  *   FS_ERR_BUDGET if it can never fit, FS_ERR_BUSY if the queue is full.
+ *   A follow-up names its parent's ticket in `parent`; a parent that kept its
+ *   spectrum with keep = k accepts at most k follow-ups (the spectrum is
+ *   released once k have completed): a further one, or one whose parent kept
+ *   nothing, is rejected with FS_ERR_ARG.  A queued follow-up whose parent's
+ *   spectrum is gone finishes with latency -1 and fs_serve_poll reports
+ *   FS_ERR_ARG.
  * fs_serve_replay: open-loop driver -- enqueue reqs[i] at arrival_s[i]
  *   seconds after the call (blocking until the last is enqueued); a
  *   follow-up's `parent` is given as (index of its parent in reqs) + 1.
@@ -343,7 +349,8 @@ fs_status fs_batch_wait(uint64_t ticket, int timeout_us);
  *   timeout_us (< 0: unbounded) for one; *n_done receives the count.
  * fs_serve_latency: enqueue -> observed completion, microseconds.
  * fs_serve_stats: batches, completed, max in flight, batches launched while
- *   another was in flight, peak bytes used, bytes used, queued, kept.
+ *   another was in flight, peak bytes used, bytes used, queued, kept,
+ *   failed (requests finished without running).
  * fs_serve_stop: drain the queue, wait for in-flight work, release memory. */
 fs_status fs_serve_start(size_t hbm_budget_bytes, int slots, int max_batch);
 fs_status fs_serve_enqueue(const fs_request *req, uint64_t *ticket_out);

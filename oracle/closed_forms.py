@@ -99,14 +99,17 @@ def gaussian_heat(blobs, D, t, nx, ny, lx, ly, x0=0.0, y0=0.0, images=2):
     over images n in [-images, images]^2; at t = 0 this is the initial field.
     """
     x, y = _grid(nx, ny, lx, ly, x0, y0)
-    out = np.zeros((ny, nx), dtype=np.float64)
-    for cx, cy, w, amp in blobs:
+    # exp(-r^2/s2) = exp(-dx^2/s2) exp(-dy^2/s2), and the sum over the image
+    # lattice factors the same way, so each blob is the outer product of its
+    # x and y image sums: u = sum_blob pref * Y_blob X_blob^T
+    xs = np.zeros((len(blobs), nx), dtype=np.float64)
+    ys = np.zeros((ny, len(blobs)), dtype=np.float64)
+    for i, (cx, cy, w, amp) in enumerate(blobs):
         s2 = float(w) ** 2 + 4.0 * float(D) * float(t)
         pref = float(amp) * float(w) ** 2 / s2
         for ix in range(-images, images + 1):
-            dx2 = (x - cx - ix * lx) ** 2
-            ex = np.exp(-dx2 / s2)
-            for iy in range(-images, images + 1):
-                dy2 = (y - cy - iy * ly) ** 2
-                out += pref * ex * np.exp(-dy2 / s2)
-    return out
+            xs[i] += np.exp(-((x[0] - cx - ix * lx) ** 2) / s2)
+        for iy in range(-images, images + 1):
+            ys[:, i] += np.exp(-((y[:, 0] - cy - iy * ly) ** 2) / s2)
+        xs[i] *= pref
+    return ys @ xs

@@ -110,6 +110,9 @@ struct Server {
   std::condition_variable cv, done_cv;
   std::deque<Req> queue;
   std::unordered_map<uint64_t, Kept> kept;
+  // follow-ups a keep request may still receive (ticket -> keep minus the
+  // follow-ups enqueued so far); an entry leaves the map at zero
+  std::unordered_map<uint64_t, int> follow_left;
   std::deque<uint64_t> done_q;
   std::unordered_map<uint64_t, double> lat_us;
   std::deque<uint64_t> lat_order;
@@ -125,7 +128,7 @@ struct Server {
   size_t queue_cap = 1u << 20;
   long long direct_min_points = 2048LL * 2048LL;  // grids this large run as standalone passes
   // statistics
-  uint64_t n_batches = 0, n_done = 0, max_inflight = 0, overlap_batches = 0;
+  uint64_t n_batches = 0, n_done = 0, max_inflight = 0, overlap_batches = 0, n_failed = 0;
   fs_status last_error = FS_OK;
 };
 
@@ -181,6 +184,17 @@ void harvest_locked(Server *S) {
   if (!S->done_q.empty()) S->done_cv.notify_all();
 }
 
+// Is request `ticket` still queued or in flight (a parent whose spectrum is
+// not kept yet)?
+bool parent_pending_locked(const Server *S, uint64_t ticket) {
+  for (const Req &w : S->queue)
+    if (w.ticket == ticket) return true;
+  for (const Flight &f : S->flights)
+    for (const Req &w : f.reqs)
+      if (w.ticket == ticket) return true;
+  return false;
+}
+
 // Form and launch one batch on a free slot; returns true if one was launched.
 bool launch_one_locked(Server *S) {
   int slot = -1;
@@ -204,6 +218,21 @@ bool launch_one_locked(Server *S) {
     size_t credit = 0;  // a follow-up spends the workspace its parent reserved
     if (q.r.parent) {
       auto k = S->kept.find(q.r.parent);
+      if (k == S->kept.end() && !parent_pending_locked(S, q.r.parent)) {
+        // the parent's spectrum is gone (it was released after its declared
+        // follow-ups): this request can never run, so finish it with an error
+        // instead of leaving it in the queue (fs_serve_stop waits for an empty
+        // queue)
+        S->done_q.push_back(q.ticket);
+        S->lat_us[q.ticket] = -1.0;
+        S->lat_order.push_back(q.ticket);
+        ++S->n_done;
+        ++S->n_failed;
+        S->last_error = FS_ERR_ARG;
+        it = S->queue.erase(it);
+        S->done_cv.notify_all();
+        continue;
+      }
       if (k == S->kept.end() || !k->second.ready) {
         ++it;  // its spectrum is not on the device yet
         continue;
@@ -342,18 +371,24 @@ static fs_status enqueue_locked(Server *S, const fs_request *req, clk::time_poin
   q.r = r;
   q.arrival = arrival;
   const bool adv = r.op == FS_OP_DIFFUSION_ADVANCE || r.op == FS_OP_WAVE_ADVANCE;
+  auto left = S->follow_left.end();
   if (adv && r.parent) {
+    // at most `keep` follow-ups per kept spectrum: the spectrum (and the
+    // workspace its parent reserved) is released after that many complete
+    left = S->follow_left.find(r.parent);
+    if (left == S->follow_left.end() || left->second <= 0)
+      return set_error(FS_ERR_ARG,
+                       "fs_serve_enqueue: parent spectrum is not kept, or all its declared follow-ups were enqueued");
     auto k = S->kept.find(r.parent);
-    bool queued_parent = false;
-    if (k == S->kept.end())
-      for (auto &w : S->queue)
-        if (w.ticket == r.parent) queued_parent = true;
-    if (k == S->kept.end() && !queued_parent)
-      return set_error(FS_ERR_ARG, "fs_serve_enqueue: parent spectrum is not kept");
     fs_plan p = k != S->kept.end() ? k->second.st.plan : nullptr;
     if (!p)
       for (auto &w : S->queue)
         if (w.ticket == r.parent) p = w.r.plan;
+    if (!p)
+      for (auto &f : S->flights)
+        for (auto &w : f.reqs)
+          if (w.ticket == r.parent) p = w.r.plan;
+    if (!p) return set_error(FS_ERR_ARG, "fs_serve_enqueue: parent spectrum is not kept");
     q.r.plan = p;
     fs_state_s probe{};
     probe.plan = p;
@@ -387,6 +422,8 @@ static fs_status enqueue_locked(Server *S, const fs_request *req, clk::time_poin
     return set_error(FS_ERR_BUDGET, "fs_serve_enqueue: request exceeds the budget");
   if (S->queue.size() >= S->queue_cap) return set_error(FS_ERR_BUSY, "fs_serve_enqueue: queue full");
   q.ticket = S->next_ticket++;
+  if (left != S->follow_left.end() && --left->second <= 0) S->follow_left.erase(left);
+  if (q.keep && r.keep > 0) S->follow_left[q.ticket] = r.keep;
   S->queue.push_back(q);
   if (ticket_out) *ticket_out = q.ticket;
   S->cv.notify_one();
@@ -468,7 +505,7 @@ extern "C" fs_status fs_serve_stats(uint64_t *out, int cap) {
   if (!S || !out) return set_error(FS_ERR_ARG, "fs_serve_stats: server not started / NULL");
   std::lock_guard<std::mutex> lk(S->mu);
   const uint64_t v[] = {S->n_batches, S->n_done, S->max_inflight, S->overlap_batches, S->peak_used, S->used,
-                        S->queue.size(), S->kept.size()};
+                        S->queue.size(), S->kept.size(), S->n_failed};
   for (int i = 0; i < cap && i < (int)(sizeof v / sizeof v[0]); ++i) out[i] = v[i];
   return FS_OK;
 }

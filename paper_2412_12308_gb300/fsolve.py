@@ -165,6 +165,63 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+# Geometry of the handles this binding created: plan -> (nx, ny, dtype), and
+# state / RK4 integrator -> its plan, so that every field argument can be
+# checked against the grid before its pointer reaches the library.
+_plans = {}
+_owner = {}
+
+
+def _key(h):
+    return h.value if isinstance(h, ctypes.c_void_p) else h
+
+
+def _plan_geom(plan):
+    k = _key(plan)
+    if k is None:
+        return None
+    g = _plans.get(k)
+    if g is None:
+        info = fs_plan_info(plan)
+        g = (info["nx"], info["ny"], info["dtype"])
+        _plans[k] = g
+    return g
+
+
+def _owner_geom(h):
+    plan = _owner.get(_key(h))
+    return None if plan is None else _plan_geom(plan)
+
+
+def _torch_dtype(dtype, cplx):
+    import torch
+
+    return {(FS_F32, False): torch.float32, (FS_F64, False): torch.float64,
+            (FS_F32, True): torch.complex64, (FS_F64, True): torch.complex128}[(dtype, bool(cplx))]
+
+
+def _field(t, geom, where, name, cplx=False):
+    """Device pointer of a field argument, after checking that the tensor is a
+    contiguous [ny][nx] field of the plan's element type in device memory (or
+    host memory pinned by CUDA); raw integer pointers are passed unchecked."""
+    if t is None or isinstance(t, int) or geom is None:
+        return _ptr(t)
+    nx, ny, dtype = geom
+    want = _torch_dtype(dtype, cplx)
+    bad = None
+    if t.dtype != want:
+        bad = f"dtype {t.dtype}, the plan needs {want}"
+    elif t.numel() != nx * ny:
+        bad = f"{t.numel()} elements, the grid has {ny} x {nx}"
+    elif not t.is_contiguous():
+        bad = "not contiguous"
+    elif not (t.is_cuda or t.is_pinned()):
+        bad = "neither device memory nor pinned host memory"
+    if bad:
+        raise FsError(-1, where, f"{name}: {bad}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream(s):
     if s is None:
         import torch
@@ -181,12 +238,14 @@ def fs_plan_create(nx, ny, lx, ly, dtype):
     h = _vp()
     _check(_lib.fs_plan_create(int(nx), int(ny), float(lx), float(ly), int(dtype), ctypes.byref(h)),
            "fs_plan_create")
+    _plans[h.value] = (int(nx), int(ny), int(dtype))
     return h
 
 
 def fs_plan_destroy(plan):
     load()
     _check(_lib.fs_plan_destroy(plan), "fs_plan_destroy")
+    _plans.pop(_key(plan), None)
 
 
 def fs_plan_info(plan):
@@ -201,25 +260,29 @@ def fs_plan_info(plan):
 
 def fs_poisson_solve(plan, f, u, stream=None):
     load()
-    _check(_lib.fs_poisson_solve(plan, _ptr(f), _ptr(u), _stream(stream)), "fs_poisson_solve")
+    g, w = _plan_geom(plan), "fs_poisson_solve"
+    _check(_lib.fs_poisson_solve(plan, _field(f, g, w, "f"), _field(u, g, w, "u"), _stream(stream)), w)
 
 
 def fs_poisson_solve_static(nx, ny, lx, ly, f, u, stream=None):
     load()
-    _check(_lib.fs_poisson_solve_static(int(nx), int(ny), float(lx), float(ly), _ptr(f), _ptr(u),
-                                        _stream(stream)), "fs_poisson_solve_static")
+    g, w = (int(nx), int(ny), FS_F32), "fs_poisson_solve_static"
+    _check(_lib.fs_poisson_solve_static(int(nx), int(ny), float(lx), float(ly), _field(f, g, w, "f"),
+                                        _field(u, g, w, "u"), _stream(stream)), w)
 
 
 def fs_diffusion_solve(plan, u0, D, t, u, stream=None):
     load()
-    _check(_lib.fs_diffusion_solve(plan, _ptr(u0), float(D), float(t), _ptr(u), _stream(stream)),
-           "fs_diffusion_solve")
+    g, w = _plan_geom(plan), "fs_diffusion_solve"
+    _check(_lib.fs_diffusion_solve(plan, _field(u0, g, w, "u0"), float(D), float(t), _field(u, g, w, "u"),
+                                   _stream(stream)), w)
 
 
 def fs_wave_solve(plan, u0, v0, c, t, u, stream=None):
     load()
-    _check(_lib.fs_wave_solve(plan, _ptr(u0), _ptr(v0), float(c), float(t), _ptr(u), _stream(stream)),
-           "fs_wave_solve")
+    g, w = _plan_geom(plan), "fs_wave_solve"
+    _check(_lib.fs_wave_solve(plan, _field(u0, g, w, "u0"), _field(v0, g, w, "v0"), float(c), float(t),
+                              _field(u, g, w, "u"), _stream(stream)), w)
 
 
 def fs_tune(nx, ny, lx, ly, dtype, reps=10):
@@ -265,43 +328,52 @@ def fs_plan_tiles(plan):
 def fs_poisson_solve_c(plan, f, u, stream=None):
     """Complex fields: f, u are complex64/complex128 tensors [ny][nx]."""
     load()
-    _check(_lib.fs_poisson_solve_c(plan, _ptr(f), _ptr(u), _stream(stream)), "fs_poisson_solve_c")
+    g, w = _plan_geom(plan), "fs_poisson_solve_c"
+    _check(_lib.fs_poisson_solve_c(plan, _field(f, g, w, "f", True), _field(u, g, w, "u", True),
+                                   _stream(stream)), w)
 
 
 def fs_diffusion_solve_c(plan, u0, D, t, u, stream=None):
     load()
-    _check(_lib.fs_diffusion_solve_c(plan, _ptr(u0), float(D), float(t), _ptr(u), _stream(stream)),
-           "fs_diffusion_solve_c")
+    g, w = _plan_geom(plan), "fs_diffusion_solve_c"
+    _check(_lib.fs_diffusion_solve_c(plan, _field(u0, g, w, "u0", True), float(D), float(t),
+                                     _field(u, g, w, "u", True), _stream(stream)), w)
 
 
 def fs_wave_solve_c(plan, u0, v0, c, t, u, stream=None):
     load()
-    _check(_lib.fs_wave_solve_c(plan, _ptr(u0), _ptr(v0), float(c), float(t), _ptr(u), _stream(stream)),
-           "fs_wave_solve_c")
+    g, w = _plan_geom(plan), "fs_wave_solve_c"
+    _check(_lib.fs_wave_solve_c(plan, _field(u0, g, w, "u0", True), _field(v0, g, w, "v0", True), float(c),
+                                float(t), _field(u, g, w, "u", True), _stream(stream)), w)
 
 
 def fs_state_create(plan, u0, v0=None, stream=None):
     load()
     h = _vp()
-    _check(_lib.fs_state_create(plan, _ptr(u0), _ptr(v0), _stream(stream), ctypes.byref(h)),
-           "fs_state_create")
+    g, w = _plan_geom(plan), "fs_state_create"
+    _check(_lib.fs_state_create(plan, _field(u0, g, w, "u0"), _field(v0, g, w, "v0"), _stream(stream),
+                                ctypes.byref(h)), w)
+    _owner[h.value] = plan
     return h
 
 
 def fs_state_destroy(state):
     load()
     _check(_lib.fs_state_destroy(state), "fs_state_destroy")
+    _owner.pop(_key(state), None)
 
 
 def fs_state_reset(state, u0, v0=None, stream=None):
     load()
-    _check(_lib.fs_state_reset(state, _ptr(u0), _ptr(v0), _stream(stream)), "fs_state_reset")
+    g, w = _owner_geom(state), "fs_state_reset"
+    _check(_lib.fs_state_reset(state, _field(u0, g, w, "u0"), _field(v0, g, w, "v0"), _stream(stream)), w)
 
 
 def fs_state_set_source(state, s, stream=None):
     """Attach a constant source field (None detaches it) to a kept state."""
     load()
-    _check(_lib.fs_state_set_source(state, _ptr(s), _stream(stream)), "fs_state_set_source")
+    g, w = _owner_geom(state), "fs_state_set_source"
+    _check(_lib.fs_state_set_source(state, _field(s, g, w, "s"), _stream(stream)), w)
 
 
 def fs_rk4_create(plan, c, src, u0=None, v0=None, t0=0.0, stream=None):
@@ -312,8 +384,10 @@ def fs_rk4_create(plan, c, src, u0=None, v0=None, t0=0.0, stream=None):
     s = FsOrbitSource(float(src.A), float(src.sigma), float(src.radius), float(src.Omega), float(src.gamma),
                       float(src.x_min), float(src.y_min))
     h = _vp()
-    _check(_lib.fs_rk4_create(plan, float(c), ctypes.byref(s), _ptr(u0), _ptr(v0), float(t0), _stream(stream),
-                              ctypes.byref(h)), "fs_rk4_create")
+    g, w = _plan_geom(plan), "fs_rk4_create"
+    _check(_lib.fs_rk4_create(plan, float(c), ctypes.byref(s), _field(u0, g, w, "u0"), _field(v0, g, w, "v0"),
+                              float(t0), _stream(stream), ctypes.byref(h)), w)
+    _owner[h.value] = plan
     return h
 
 
@@ -324,7 +398,8 @@ def fs_rk4_step(rk, dt, nsteps, stream=None):
 
 def fs_rk4_output(rk, u_out, v_out=None, stream=None):
     load()
-    _check(_lib.fs_rk4_output(rk, _ptr(u_out), _ptr(v_out), _stream(stream)), "fs_rk4_output")
+    g, w = _owner_geom(rk), "fs_rk4_output"
+    _check(_lib.fs_rk4_output(rk, _field(u_out, g, w, "u_out"), _field(v_out, g, w, "v_out"), _stream(stream)), w)
 
 
 def fs_rk4_mean(rk, stream=None):
@@ -344,6 +419,7 @@ def fs_rk4_time(rk):
 def fs_rk4_destroy(rk):
     load()
     _check(_lib.fs_rk4_destroy(rk), "fs_rk4_destroy")
+    _owner.pop(_key(rk), None)
 
 
 def fs_state_save(state, stream=None):
@@ -365,25 +441,29 @@ def fs_state_load(state, data, stream=None):
 
 def fs_diffusion_advance(state, D, t, u_out, stream=None):
     load()
-    _check(_lib.fs_diffusion_advance(state, float(D), float(t), _ptr(u_out), _stream(stream)),
-           "fs_diffusion_advance")
+    g, w = _owner_geom(state), "fs_diffusion_advance"
+    _check(_lib.fs_diffusion_advance(state, float(D), float(t), _field(u_out, g, w, "u_out"), _stream(stream)), w)
 
 
 def fs_wave_advance(state, c, t, u_out, v_out=None, stream=None):
     load()
-    _check(_lib.fs_wave_advance(state, float(c), float(t), _ptr(u_out), _ptr(v_out), _stream(stream)),
-           "fs_wave_advance")
+    g, w = _owner_geom(state), "fs_wave_advance"
+    _check(_lib.fs_wave_advance(state, float(c), float(t), _field(u_out, g, w, "u_out"),
+                                _field(v_out, g, w, "v_out"), _stream(stream)), w)
 
 
 def fs_request(op, plan=None, state=None, in_u=None, in_v=None, out_u=None, out_v=None, D=0.0, c=0.0, t=0.0,
                keep=0, parent=0):
     """Marshal one batch / serving request (tensors -> device pointers)."""
 
-    def p(x):
-        return None if x is None else (x if isinstance(x, int) else x.data_ptr())
+    geom = _plan_geom(plan) if plan is not None else (_owner_geom(state) if state is not None else None)
 
-    return FsRequest(int(op), plan, state, p(in_u), p(in_v), p(out_u), p(out_v), float(D), float(c), float(t),
-                     int(keep), int(parent))
+    def p(x, name):
+        v = _field(x, geom, "fs_request", name)
+        return v.value if isinstance(v, ctypes.c_void_p) else v
+
+    return FsRequest(int(op), plan, state, p(in_u, "in_u"), p(in_v, "in_v"), p(out_u, "out_u"), p(out_v, "out_v"),
+                     float(D), float(c), float(t), int(keep), int(parent))
 
 
 def fs_request_array(reqs):
@@ -406,7 +486,7 @@ def fs_batch_wait(ticket, timeout_us=-1):
 
 
 SERVE_STATS = ("batches", "completed", "max_in_flight", "overlapped_batches", "peak_bytes", "bytes_used",
-               "queued", "kept")
+               "queued", "kept", "failed")
 
 
 def fs_serve_start(hbm_budget_bytes, slots=2, max_batch=64):

@@ -24,7 +24,7 @@ def test_paper_mean_conservation_bound():
 
     facts = load_facts()
     assert pins.pin_diffusion_invariants() <= facts["diffusion_mean_conservation_rel"]
-    assert pins.pin_wave_invariants() <= 10 * facts["wave_mean_conservation_rel"]
+    assert pins.pin_wave_invariants() <= facts["wave_mean_conservation_rel"]
 
 
 def test_hand_dft4():

@@ -257,3 +257,43 @@ def test_diffusion_heavy_decay_normwise(gpu_lib):
             got = host(ud)
         den = max(np.linalg.norm(want), np.linalg.norm(f))
         assert np.linalg.norm(got - want) / den <= 1e-5, (D, t)
+
+
+@pytest.mark.parametrize("nx,ny", [(2048, 2048), (4096, 4096), (8192, 8192), (8192, 640)])
+def test_large_grids_fp64_closed_forms(gpu_lib, nx, ny):
+    """The FP64 path on long axes (register tiles of 8 up to length 4096 and 16
+    at 8192), square and rectangular: every operator, one-shot solves and
+    advances from a kept spectrum, against the mode-sum closed forms on the
+    whole grid at the FP64 bar rel-L2 <= 1e-12 (Eq. SolutionPoisson,
+    Eq. solCalorFourier, Eq. OmegaNonZero and its time derivative)."""
+    rng = np.random.default_rng(3 * nx + ny)
+    modes = wl.draw_modes(rng, 8, 40)
+    f = wl.mode_sum(modes, nx, ny, 1.0, 1.0)
+    tol = TOL[1]
+    with Plan(gpu_lib, nx, ny, 1.0, 1.0, 1) as p:
+        fd = p.dev(f)
+        ud = torch.full_like(fd, float("nan"))
+        vd = torch.full_like(fd, float("nan"))
+        gpu_lib.fs_poisson_solve(p.h, fd, ud)
+        assert rel(host(ud), cf.poisson_modes(modes, nx, ny, 1.0, 1.0)) <= tol
+        D, t = 1e-5, 0.5
+        u_d = cf.diffusion_modes(modes, D, t, nx, ny, 1.0, 1.0)
+        gpu_lib.fs_diffusion_solve(p.h, fd, D, t, ud)
+        assert rel(host(ud), u_d) <= tol
+        st = gpu_lib.fs_state_create(p.h, fd)
+        try:
+            gpu_lib.fs_diffusion_advance(st, D, t, ud)
+            assert rel(host(ud), u_d) <= tol
+            del u_d
+            u_w, v_w = cf.wave_modes(modes, 1.3, 0.3, nx, ny, 1.0, 1.0, want_v=True)
+            gpu_lib.fs_wave_advance(st, 1.3, 0.3, ud, vd)
+            assert rel(host(ud), u_w) <= tol
+            assert rel(host(vd), v_w) <= tol
+            del u_w, v_w
+            u_w = cf.wave_modes(modes, 1.0, 1.9, nx, ny, 1.0, 1.0)
+            gpu_lib.fs_wave_advance(st, 1.0, 1.9, ud)
+            assert rel(host(ud), u_w) <= tol
+            gpu_lib.fs_wave_solve(p.h, fd, None, 1.0, 1.9, ud)
+            assert rel(host(ud), u_w) <= tol
+        finally:
+            gpu_lib.fs_state_destroy(st)

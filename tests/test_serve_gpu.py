@@ -25,11 +25,11 @@ OPS = {"poisson": fsolve.FS_OP_POISSON, "diffusion": fsolve.FS_OP_DIFFUSION, "wa
 class Stream:
     """Seeded request stream with device buffers (each request its own output)."""
 
-    def __init__(self, count, sizes, seed):
+    def __init__(self, count, sizes, seed, explicit=False):
         rng = np.random.default_rng(seed)
         self.plans, self.items = {}, []
         for i in range(count):
-            n = int(sizes[int(rng.integers(0, len(sizes)))])
+            n = int(sizes[i % len(sizes)]) if explicit else int(sizes[int(rng.integers(0, len(sizes)))])
             op = ("poisson", "diffusion", "wave")[int(rng.integers(0, 3))]
             p = wl.Problem(op=op, n=n, modes=wl.draw_modes(rng, 8, min(16, n // 2 - 1)))
             if op == "diffusion":
@@ -81,12 +81,12 @@ def _snapshot(items):
     return [(it["out"].clone(), None if it["follow"] is None else it["follow"].clone()) for it in items]
 
 
-def test_alone_vs_mix_and_oracle(gpu_lib):
-    S = Stream(40, (128, 160, 256, 320, 512, 640, 1024), seed=3)
+def _alone_vs_mix(S, budget, slots, max_batch, window_s):
+    """Each request alone on an idle server, then all of them in an open-loop
+    mix arriving within `window_s`: identical results bit for bit."""
     reqs, where = S.requests()
-    fsolve.fs_serve_start(4 << 30, slots=3, max_batch=16)
+    fsolve.fs_serve_start(budget, slots=slots, max_batch=max_batch)
     try:
-        # alone: each request (and its follow-up) on an idle server
         i = 0
         while i < len(reqs):
             k = 2 if (i + 1 < len(reqs) and reqs[i + 1].parent) else 1
@@ -99,21 +99,57 @@ def test_alone_vs_mix_and_oracle(gpu_lib):
             it["out"].fill_(float("nan"))
             if it["follow"] is not None:
                 it["follow"].fill_(float("nan"))
-        # the mix: all requests arrive within ~2 ms
-        arrivals = np.sort(np.random.default_rng(1).uniform(0.0, 0.002, len(reqs)))
-        tk = fsolve.fs_serve_replay(reqs, list(arrivals))  # a follow-up still follows its parent
-        _drain(tk)
+        arrivals = np.sort(np.random.default_rng(1).uniform(0.0, window_s, len(reqs)))
+        tk = fsolve.fs_serve_replay(reqs, list(arrivals))
+        _drain(tk, timeout_s=120.0)
         stats = fsolve.fs_serve_stats()
+        for t in tk:
+            assert fsolve.fs_serve_latency(t) > 0.0
         mixed = _snapshot(S.items)
         for (a_out, a_fol), (m_out, m_fol) in zip(alone, mixed):
             assert torch.equal(a_out, m_out)
             if a_fol is not None:
                 assert torch.equal(a_fol, m_fol)
-        assert stats["max_in_flight"] >= 2, stats
-        for t in tk:
-            assert fsolve.fs_serve_latency(t) > 0.0
+        return stats, tk
     finally:
         fsolve.fs_serve_stop()
+
+
+def test_alone_vs_mix_large_grids(gpu_lib):
+    """Grids of 2048^2 and more run as standalone passes inside their slot;
+    they too give the same bits alone and next to small requests that share
+    the persistent launch."""
+    S = Stream(9, (2048, 256, 4096, 512, 1024, 2048, 128, 4096, 640), seed=17, explicit=True)
+    stats, _ = _alone_vs_mix(S, 8 << 30, 3, 8, 0.003)
+    assert stats["max_in_flight"] >= 2, stats
+    for it in S.items:
+        assert torch.isfinite(it["out"]).all()
+    # the large grids against their closed forms (mode sums: exact on the grid)
+    from oracle import closed_forms as cf
+
+    for it in S.items:
+        p = it["p"]
+        if p.n < 2048:
+            continue
+        if p.op == "poisson":
+            want = cf.poisson_modes(p.modes, p.n, p.n, 1.0, 1.0)
+            den = np.linalg.norm(want)
+        elif p.op == "diffusion":
+            want = cf.diffusion_modes(p.modes, p.D, p.t, p.n, p.n, 1.0, 1.0)
+            den = max(np.linalg.norm(want), np.linalg.norm(it["f"].double().cpu().numpy()))
+        else:
+            want = cf.wave_modes(p.modes, p.c, p.t, p.n, p.n, 1.0, 1.0)
+            den = np.linalg.norm(want)
+        got = it["out"].double().cpu().numpy()
+        assert np.linalg.norm(got - want) / den <= 1e-5, (p.op, p.n)
+    S.close()
+
+
+def test_alone_vs_mix_and_oracle(gpu_lib):
+    S = Stream(40, (128, 160, 256, 320, 512, 640, 1024), seed=3)
+    # the mix: all requests arrive within ~2 ms
+    stats, tk = _alone_vs_mix(S, 4 << 30, 3, 16, 0.002)
+    assert stats["max_in_flight"] >= 2, stats
     # oracle on a sample (first output and follow-up of every fourth item)
     for it in S.items[::4]:
         p = it["p"]
@@ -186,4 +222,40 @@ def test_rejections(gpu_lib):
             fsolve.fs_serve_enqueue(adv)
     finally:
         fsolve.fs_serve_stop()
+    S.close()
+
+
+def test_followups_beyond_keep_are_rejected(gpu_lib):
+    """A kept spectrum serves exactly `keep` follow-ups: the one after them is
+    rejected at enqueue (it would otherwise read a released spectrum or wait
+    forever), and the server still drains and stops."""
+    S = Stream(1, (256,), seed=21)
+    it = S.items[0]
+    f = it["f"]
+    out = [torch.empty_like(f) for _ in range(3)]
+    fsolve.fs_serve_start(1 << 30, slots=2, max_batch=4)
+    try:
+        parent = fsolve.fs_serve_enqueue(fsolve.fs_request(fsolve.FS_OP_DIFFUSION, plan=S.plans[256], in_u=f,
+                                                           out_u=out[0], D=0.01, t=0.2, keep=2))
+        tk = [parent]
+        for j in (1, 2):
+            tk.append(fsolve.fs_serve_enqueue(fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, out_u=out[j],
+                                                                D=0.01, t=0.2 + 0.1 * j, parent=parent)))
+        with pytest.raises(fsolve.FsError) as ei:
+            fsolve.fs_serve_enqueue(fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, out_u=out[1], D=0.01, t=0.9,
+                                                      parent=parent))
+        assert ei.value.status == -1
+        _drain(tk)
+        # every declared follow-up done: the spectrum is released, later ones are refused
+        with pytest.raises(fsolve.FsError):
+            fsolve.fs_serve_enqueue(fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, out_u=out[1], D=0.01, t=0.9,
+                                                      parent=parent))
+        st = fsolve.fs_serve_stats()
+        assert st["kept"] == 0 and st["bytes_used"] == 0 and st["failed"] == 0
+    finally:
+        fsolve.fs_serve_stop()  # returns: nothing is left waiting in the queue
+    fh = f.double().cpu().numpy()
+    for j, t in ((1, 0.3), (2, 0.4)):
+        want = oracle.diffusion(fh, 0.01, t, 1.0, 1.0)
+        assert np.linalg.norm(out[j].double().cpu().numpy() - want) / np.linalg.norm(want) <= 1e-5
     S.close()

@@ -5,8 +5,8 @@
   (exact for mode sums), rel-L2 <= 1e-5 (normwise for strongly decayed
   diffusion, the largest diffusion multiplier being 1).
 * Wave 4096^2 with a Gaussian pulse plus white noise, 50 snapshots from one
-  kept spectrum in one batch: every 10th snapshot and t = 1 against the float64
-  oracle (rel-L2 <= 1e-5), mean and energy invariants on all 50.
+  kept spectrum in one batch: every 10th snapshot (t = 0.2, 0.4, ..., 1)
+  against the float64 oracle (rel-L2 <= 1e-5), the mean invariant on all 50.
 * Diffusion 1024^2, 100 output times: every output against the periodic heat
   kernel (exact on this grid: the narrowest blob's spectrum is e^-164 at
   Nyquist), rel-L2 <= 1e-5.
@@ -97,7 +97,8 @@ def test_diffusion_1024_heat_kernel_all_times(gpu_lib):
                 for j, t in enumerate(times)]
         tk = fsolve.fs_batch_submit(reqs)
         fsolve.fs_batch_wait(tk, 60_000_000)
-        for j in range(0, len(times), 11):
+        assert len(times) == 100
+        for j in range(len(times)):
             want = cf.gaussian_heat(blobs, D, float(times[j]), n, n, lx, ly, images=1)
             got = outs[j].double().cpu().numpy()
             err = float(np.linalg.norm(got - want) / np.linalg.norm(want))

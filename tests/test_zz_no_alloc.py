@@ -2,9 +2,9 @@
 
 fs_poisson_solve_static serves callers that may not allocate device memory
 while they run; its scratch is a fixed array inside the library.  It must
-give the same answer as the plan-based fs_poisson_solve (within the FP32
-bar used everywhere, rel-L2 <= 1e-5) on consecutive calls that reuse the
-shared array, must not change the device's free memory once set up, and
+give the same answer as the plan-based fs_poisson_solve and as the float64
+oracle (within the FP32 bar used everywhere, rel-L2 <= 1e-5) on consecutive
+calls that reuse the shared array, must not change the device's free memory once set up, and
 must refuse grids beyond its fixed 1024 x 1024 limit.
 
 This file is collected last so that a run stopping at the first failure has
@@ -45,6 +45,24 @@ def test_static_matches_plan_entry_point(gpu_lib, nx, ny, lx, ly):
             assert _rel(out, ref) <= 1e-5
     finally:
         fsolve.fs_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("nx,ny,lx,ly", [(64, 64, 1.0, 1.0), (96, 40, 2.0, 0.7), (1024, 256, 1.0, 1.0)])
+def test_static_matches_oracle(gpu_lib, nx, ny, lx, ly):
+    """The static entry point shares its pass kernels with fs_poisson_solve, so
+    it is also checked against the float64 oracle (an independent direct DFT,
+    Eq. SolutionPoisson) on the same float32-rounded input."""
+    import oracle
+
+    rng = np.random.default_rng(7 * nx + ny)
+    f_host = rng.standard_normal((ny, nx)).astype(np.float32)
+    want = oracle.poisson(f_host.astype(np.float64), lx, ly)
+    f = torch.tensor(f_host, device="cuda")
+    for _ in range(2):
+        out = torch.full_like(f, float("nan"))
+        fsolve.fs_poisson_solve_static(nx, ny, lx, ly, f, out)
+        got = out.double().cpu().numpy()
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-5
 
 
 def test_static_allocates_nothing_per_call(gpu_lib):
