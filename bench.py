@@ -14,8 +14,16 @@ Arms:
   --impl reference   the float64 CPU oracle on the host cores (the whole step
                      of the same workload: 1 forward 2D DFT + 100 outputs)
 
+Beside the headline the line carries `legs`, further workloads of the same
+metric, each with its own roofline: the one-shot Poisson solve on 4096^2 with
+the plain per-solve torch.fft path beside it, the 4096^2 wave with 50
+snapshots from one kept spectrum, and the 512-problem uneven batch.  Their
+accuracy against the float64 oracle (or exact closed forms) is computed in
+the CPU-baseline leg.  `--leg NAME` runs one of them alone (for profilers).
+
 Multi-GPU (torchrun, one rank per GPU): every rank runs its own copy of the
-workload (replicas, weak scaling); the time is the max over ranks.
+headline workload (replicas, weak scaling); the 512-problem batch is split
+across ranks (replicas.shard); times are the max over ranks.
 """
 
 import argparse
@@ -49,6 +57,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving leg")
     ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--legs", default=",".join(LEGS),
+                    help="comma-separated extra workloads reported beside the headline ('' for none)")
+    ap.add_argument("--leg", choices=sorted(LEG_FNS), default=None,
+                    help="run only this workload and print its JSON (e.g. under a profiler)")
     return ap.parse_args()
 
 
@@ -206,12 +218,12 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 
 
 # ----------------------------------------------------------------------------- ours
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one batch launch
-# of this workload from one ncu capture (profiles/k_batch_diffusion_1024.md),
-# valid only for the CUDA sources it was taken on: any change to them makes
-# the reported traffic null until a new capture.
-TRAFFIC_CAPTURE = {"kernel": "batch", "bytes": 165655552 + 784329984,
-                   "sources_sha256": "aaa621d0c2bd51be45f63e4e096a682399e9ab06d9e17ec4d3f090c5497f29bb"}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# workload's kernels from ncu captures (summaries under profiles/), valid only
+# for the CUDA sources they were taken on: any change to the sources makes the
+# reported traffic null until a new capture.
+# (workload, kernel class) -> {"bytes": DRAM bytes per launch, "sources_sha256": digest of csrc/}
+TRAFFIC_CAPTURES = {}
 
 
 def _csrc_digest():
@@ -228,6 +240,305 @@ def _csrc_digest():
     return h.hexdigest()
 
 
+# ----------------------------------------------------------------------------- legs
+# Further workloads of the same metric, reported beside the headline (each a
+# configuration of the measured set): the one-shot 4096^2 Poisson solve with
+# the plain per-solve comparator, the 4096^2 wave with 50 snapshots from one
+# kept spectrum, and the 512-problem uneven batch (sharded across ranks).
+LEGS = ("poisson_4096", "wave_4096_snapshots", "batch_mix_512")
+
+
+def _spec_bytes(n, esz=4):
+    return (n // 2 + 1) * n * 2 * esz
+
+
+def _events_ms(torch, fn, reps, flush):
+    """Device time of `reps` calls of fn, L2 flushed (untimed) before each."""
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def _kernel_us(fsolve, torch, fn, reps, flush):
+    """Mean device time per launch of each pass class (library events on the
+    launching stream) over `reps` calls of fn."""
+    fsolve.fs_profile_enable(True)
+    for _ in range(reps):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    prof = fsolve.fs_profile_report()
+    fsolve.fs_profile_enable(False)
+    return {k: (c, 1e3 * tot / c) for k, (c, tot) in prof.items() if c}
+
+
+def _roof(algo_bytes, seconds, peak, peak_src, traffic=None, **extra):
+    gbs = algo_bytes / seconds / 1e9 if seconds > 0 else 0.0
+    out = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+           "frac_of_8tbs": round(gbs / 8000.0, 4), "traffic": traffic, "peak_source": peak_src,
+           "algorithmic_bytes_per_launch": int(algo_bytes)}
+    out.update(extra)
+    return out
+
+
+def _capture_traffic(leg, kernel):
+    """DRAM bytes per launch of `kernel` in `leg` from the ncu capture listed in
+    TRAFFIC_CAPTURES, if it was taken on the current kernel sources."""
+    cap = TRAFFIC_CAPTURES.get((leg, kernel))
+    if cap and _csrc_digest() == cap["sources_sha256"]:
+        return cap["bytes"]
+    return None
+
+
+def leg_poisson_4096(ctx):
+    """One-shot Poisson solve on a 4096^2 FP32 grid (8-mode source, |k| <= 40,
+    exact closed form), one solve per call, L2 flushed between calls; beside it
+    the plain per-solve path: torch.fft.rfft2 -> multiply by -1/|k|^2 ->
+    torch.fft.irfft2 (cuFFT, separate launches)."""
+    torch, fsolve, dev, flush, reps = ctx["torch"], ctx["fsolve"], ctx["dev"], ctx["flush"], ctx["reps"]
+    from paper_2412_12308_gb300 import workloads as wl
+
+    n = 4096
+    modes = wl.draw_modes(np.random.default_rng(12313), 8, 40)
+    f = wl.mode_sum(modes, n, n, 1.0, 1.0).astype(np.float32)
+    plan = fsolve.fs_plan_create(n, n, 1.0, 1.0, fsolve.FS_F32)
+    fd = torch.tensor(f, device=dev)
+    ud = torch.empty_like(fd)
+
+    def solve():
+        fsolve.fs_poisson_solve(plan, fd, ud)
+
+    for _ in range(ctx["warmup"]):
+        solve()
+    torch.cuda.synchronize()
+    l0 = fsolve.fs_kernel_launches()
+    ms = _events_ms(torch, solve, reps, flush)
+    launches = (fsolve.fs_kernel_launches() - l0) // reps
+    kus = _kernel_us(fsolve, torch, solve, reps, flush)
+    spec, real = _spec_bytes(n), n * n * 4
+    ms_solve = statistics.mean(ms)
+    passes = {"row_r2c": real + spec, "column": 2 * spec, "row_c2r": spec + real}
+    per_pass = {k: {"us": round(kus[k][1], 3), "algorithmic_GBps": round(b / (kus[k][1] * 1e-6) / 1e9, 1),
+                    "traffic": _capture_traffic("poisson_4096", k)} for k, b in passes.items() if k in kus}
+    # plain path on the same GPU
+    kx = 2 * math.pi * torch.fft.rfftfreq(n, d=1.0 / n, device=dev).double()
+    ky = 2 * math.pi * torch.fft.fftfreq(n, d=1.0 / n, device=dev).double()
+    w2 = ky[:, None] ** 2 + kx[None, :] ** 2
+    w2[0, 0] = 1.0
+    fac = (-1.0 / w2).float()
+    fac[0, 0] = 0.0
+    up = torch.empty_like(fd)
+
+    def plain():
+        up.copy_(torch.fft.irfft2(torch.fft.rfft2(fd) * fac, s=(n, n)))
+
+    plain()
+    ms_plain = statistics.mean(_events_ms(torch, plain, reps, flush))
+    torch.cuda.synchronize()
+    res = {
+        "workload": "Poisson, periodic [0,1)^2, 4096x4096 FP32, 8-mode source |k|<=40, one solve per call",
+        "value": round(1e3 / ms_solve, 2), "unit": "solves/s", "ms_per_solve": round(ms_solve, 5),
+        "gpu_launches_per_solve": int(launches),
+        "roofline": _roof(24 * n * n, ms_solve * 1e-3, ctx["peak"], ctx["peak_src"],
+                          what="24N^2 algorithmic bytes (3 passes) per solve / solve time", passes=per_pass),
+        "plain_torch_fft": {"value": round(1e3 / ms_plain, 2), "unit": "solves/s", "ms_per_solve": round(ms_plain, 5),
+                            "what": "torch.fft.rfft2 -> FP32 multiply by -1/|k|^2 -> irfft2 (cuFFT)"},
+        "l2": "flushed between calls (256 MB write, untimed)",
+    }
+    ctx["checks"].append(("poisson_4096", "closed_form_poisson", modes, n, ud.cpu().numpy(), up.cpu().numpy()))
+    fsolve.fs_plan_destroy(plan)
+    return res
+
+
+def leg_wave_4096_snapshots(ctx):
+    """Wave u_tt = c^2 lap u on periodic [0,1)^2, 4096^2 FP32, c = 1: Gaussian
+    pulse (width 0.02) + 0.01 N(0,1) noise, v0 = 0; one step = forward
+    transform into the kept spectrum + 50 snapshots t = j/50 as one batch."""
+    torch, fsolve, dev, flush, reps = ctx["torch"], ctx["fsolve"], ctx["dev"], ctx["flush"], ctx["reps"]
+    from paper_2412_12308_gb300 import workloads as wl
+
+    u0, (lx, ly), c, times, _ = wl.wave_pulse_4096()
+    u0 = u0.astype(np.float32)
+    n = u0.shape[0]
+    plan = fsolve.fs_plan_create(n, n, lx, ly, fsolve.FS_F32)
+    ud = torch.tensor(u0, device=dev)
+    st = fsolve.fs_state_create(plan, ud)
+    outs = torch.empty((len(times), n, n), dtype=torch.float32, device=dev)
+    reqs = fsolve.fs_request_array([fsolve.fs_request(fsolve.FS_OP_WAVE_ADVANCE, state=st, out_u=outs[j], c=c,
+                                                      t=float(t)) for j, t in enumerate(times)])
+
+    def step():
+        fsolve.fs_state_reset(st, ud)
+        fsolve.fs_batch_submit(reqs)
+
+    for _ in range(ctx["warmup"]):
+        step()
+    torch.cuda.synchronize()
+    l0 = fsolve.fs_kernel_launches()
+    ms = statistics.mean(_events_ms(torch, step, reps, flush))
+    launches = (fsolve.fs_kernel_launches() - l0) // reps
+    kus = _kernel_us(fsolve, torch, step, reps, flush)
+    spec, real = _spec_bytes(n), n * n * 4
+    dom = max(kus.items(), key=lambda kv: kv[1][1])
+    algo = {"batch": len(times) * (3 * spec + real), "row_r2c": real + spec, "column": 2 * spec}.get(dom[0], 0)
+    res = {
+        "workload": "wave, periodic [0,1)^2, 4096x4096 FP32, c=1, Gaussian pulse + white noise, v0=0, "
+                    "1 forward + 50 snapshots t=j/50 per step",
+        "value": round(len(times) / (ms / 1e3), 2), "unit": "snapshots/s", "ms_per_step": round(ms, 4),
+        "gpu_launches_per_step": int(launches),
+        "roofline": _roof(algo, dom[1][1] * 1e-6, ctx["peak"], ctx["peak_src"],
+                          _capture_traffic("wave_4096_snapshots", dom[0]), kernel=dom[0],
+                          avg_launch_us=round(dom[1][1], 3),
+                          per_kernel_us={k: round(v[1], 3) for k, v in kus.items()}),
+        "l2": "flushed between steps (256 MB write, untimed)",
+    }
+    j = len(times) - 1
+    ctx["checks"].append(("wave_4096_snapshots", "oracle_wave", (u0, lx, ly, c, float(times[j])), n,
+                          outs[j].cpu().numpy(), None))
+    del outs
+    fsolve.fs_state_destroy(st)
+    fsolve.fs_plan_destroy(plan)
+    return res
+
+
+def leg_batch_mix_512(ctx):
+    """512 independent problems (operator uniform over Poisson / diffusion /
+    wave, N in {64, 80, ..., 2048}, 8-mode sources) in one persistent launch;
+    with several ranks each runs its share (replicas.shard: LPT by grid
+    points) and the time is the max over ranks."""
+    torch, fsolve, dev, flush, reps = ctx["torch"], ctx["fsolve"], ctx["dev"], ctx["flush"], ctx["reps"]
+    dist = ctx["dist"]
+    from paper_2412_12308_gb300 import replicas, workloads as wl
+
+    probs = wl.batch_mix()
+    idx = replicas.my_share([replicas.problem_cost(p.n) for p in probs], dist.rank, dist.world)
+    plans, ins, outs = {}, {}, {}
+    for i in idx:
+        p = probs[i]
+        if p.n not in plans:
+            plans[p.n] = fsolve.fs_plan_create(p.n, p.n, p.lx, p.ly, fsolve.FS_F32)
+        ins[i] = torch.tensor(p.field(np.float32), device=dev)
+        outs[i] = torch.empty_like(ins[i])
+    arr, idx2 = replicas.batch_share_requests(probs, dist.rank, dist.world, plans, ins, outs)
+    assert idx2 == idx
+
+    def step():
+        if arr is not None:
+            fsolve.fs_batch_submit(arr)
+
+    for _ in range(ctx["warmup"]):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    l0 = fsolve.fs_kernel_launches()
+    ms_local = statistics.mean(_events_ms(torch, step, reps, flush))
+    launches = (fsolve.fs_kernel_launches() - l0) // reps
+    ms = dist.max(ms_local)
+    kus = _kernel_us(fsolve, torch, step, reps, flush)
+    algo = sum(3 * (probs[i].n ** 2 * 4 + _spec_bytes(probs[i].n)) for i in idx)
+    dom = max(kus.items(), key=lambda kv: kv[1][1]) if kus else ("batch", (0, 0.0))
+    res = {
+        "workload": "512 independent problems, op ~ U{Poisson, diffusion D~U[0.01,1], wave c~U[0.5,2]}, "
+                    "N ~ U{64..2048: 2^k, 3*2^k, 5*2^k}, FP32, one persistent graph-captured launch per rank",
+        "value": round(len(probs) / (ms / 1e3), 2), "unit": "solves/s", "ms_per_batch": round(ms, 4),
+        "ranks": dist.world, "problems_this_rank": len(idx), "gpu_launches_per_batch": int(launches),
+        "roofline": _roof(algo, dom[1][1] * 1e-6, ctx["peak"], ctx["peak_src"],
+                          _capture_traffic("batch_mix_512", dom[0]), kernel=dom[0],
+                          avg_launch_us=round(dom[1][1], 3),
+                          what="sum over this rank's problems of 24N^2 (3-pass bytes) / batch launch time"),
+        "scaling": "strong (the 512 problems are split across ranks)",
+        "l2": "flushed between batches (256 MB write, untimed)",
+    }
+    sample = [i for i in idx if i % 8 == 0]
+    ctx["checks"].append(("batch_mix_512", "closed_form_batch", [probs[i] for i in sample], None,
+                          [outs[i].cpu().numpy() for i in sample], None))
+    for h in plans.values():
+        fsolve.fs_plan_destroy(h)
+    return res
+
+
+def leg_wave_advance_4096(ctx):
+    """One wave advance per call from a kept 4096^2 FP32 spectrum (the pulse of
+    the snapshot workload, t = 0.37): a column pass and a C2R pass per call.
+    With FS_COLUMN_VARIANT=bf16x3 in the environment the column pass is the
+    split-BF16 tensor-core variant."""
+    torch, fsolve, dev, flush, reps = ctx["torch"], ctx["fsolve"], ctx["dev"], ctx["flush"], ctx["reps"]
+    from paper_2412_12308_gb300 import workloads as wl
+
+    u0, (lx, ly), c, _times, _ = wl.wave_pulse_4096()
+    n = u0.shape[0]
+    plan = fsolve.fs_plan_create(n, n, lx, ly, fsolve.FS_F32)
+    ud = torch.tensor(u0.astype(np.float32), device=dev)
+    st = fsolve.fs_state_create(plan, ud)
+    out = torch.empty_like(ud)
+
+    def adv():
+        fsolve.fs_wave_advance(st, c, 0.37, out)
+
+    for _ in range(ctx["warmup"]):
+        adv()
+    torch.cuda.synchronize()
+    ms = statistics.mean(_events_ms(torch, adv, reps, flush))
+    kus = _kernel_us(fsolve, torch, adv, reps, flush)
+    res = {"workload": "wave advance from a kept 4096x4096 FP32 spectrum, one per call",
+           "value": round(1e3 / ms, 2), "unit": "advances/s", "ms_per_advance": round(ms, 5),
+           "column_variant": os.environ.get("FS_COLUMN_VARIANT", "fp32"),
+           "roofline": _roof(16 * n * n, ms * 1e-3, ctx["peak"], ctx["peak_src"],
+                             per_kernel_us={k: round(v[1], 3) for k, v in kus.items()})}
+    fsolve.fs_state_destroy(st)
+    fsolve.fs_plan_destroy(plan)
+    return res
+
+
+LEG_FNS = {"poisson_4096": leg_poisson_4096, "wave_4096_snapshots": leg_wave_4096_snapshots,
+           "batch_mix_512": leg_batch_mix_512, "wave_advance_4096": leg_wave_advance_4096}
+
+
+def leg_accuracy(checks):
+    """rel-L2 of each leg's sampled outputs against the float64 oracle or the
+    exact closed forms (part of the CPU-baseline leg: the only place here that
+    runs oracle code)."""
+    import oracle
+    from oracle import closed_forms as cf
+
+    out = {}
+    for leg, kind, data, n, got, extra in checks:
+        t0 = time.perf_counter()
+        if kind == "closed_form_poisson":
+            want = cf.poisson_modes(data, n, n, 1.0, 1.0)
+            r = {"rel_l2_vs_closed_form": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                 "plain_torch_fft_rel_l2_vs_closed_form": float(np.linalg.norm(extra - want) / np.linalg.norm(want))}
+        elif kind == "oracle_wave":
+            u0, lx, ly, c, t = data
+            U, _ = oracle.wave_spectrum(oracle.state_spectrum(u0.astype(np.float64)), None, c, t, lx, ly)
+            want = np.real(oracle.idft2(U))
+            r = {"rel_l2_vs_oracle": float(np.linalg.norm(got - want) / np.linalg.norm(want)), "t": t}
+        else:  # batch mix sample
+            worst = 0.0
+            for p, g in zip(data, got):
+                if p.op == "poisson":
+                    want = cf.poisson_modes(p.modes, p.n, p.n, p.lx, p.ly)
+                    den = np.linalg.norm(want)
+                elif p.op == "diffusion":
+                    want = cf.diffusion_modes(p.modes, p.D, p.t, p.n, p.n, p.lx, p.ly)
+                    den = max(np.linalg.norm(want), np.linalg.norm(p.field(np.float32).astype(np.float64)))
+                else:
+                    want = cf.wave_modes(p.modes, p.c, p.t, p.n, p.n, p.lx, p.ly)
+                    den = np.linalg.norm(want)
+                worst = max(worst, float(np.linalg.norm(g - want) / den))
+            r = {"rel_l2_vs_closed_form_max": worst, "problems_checked": len(data)}
+        r["check_seconds"] = round(time.perf_counter() - t0, 2)
+        out[leg] = r
+    return out
+
+
 def run_ours(args, dist):
     import torch
 
@@ -236,13 +547,24 @@ def run_ours(args, dist):
     torch.cuda.set_device(dist.local)
     dist.init("nccl")
     fsolve.load()
-    u0, blobs, lx, ly, D, times = workload()
     dev = torch.device("cuda", dist.local)
+    peak, peak_src = peaks()
+    ctx = {"torch": torch, "fsolve": fsolve, "dev": dev, "dist": dist, "reps": max(3, args.steps),
+           "warmup": args.warmup, "peak": peak, "peak_src": peak_src, "checks": [],
+           "flush": torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)}
+    if args.leg:
+        # one workload alone (profiling runs): its JSON only
+        res = LEG_FNS[args.leg](ctx)
+        if dist.rank == 0:
+            print(json.dumps({"leg": args.leg, **res}), flush=True)
+        dist.close()
+        return
+    u0, blobs, lx, ly, D, times = workload()
     plan = fsolve.fs_plan_create(N, N, lx, ly, fsolve.FS_F32)
     u0d = torch.tensor(u0, device=dev)
     out = torch.empty((len(times), N, N), dtype=torch.float32, device=dev)
     state = fsolve.fs_state_create(plan, u0d)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    flush = ctx["flush"]  # 256 MB > L2
     ts = [float(t) for t in times]
     reqs = fsolve.fs_request_array([fsolve.fs_request(fsolve.FS_OP_DIFFUSION_ADVANCE, state=state, out_u=out[j],
                                                       D=D, t=t) for j, t in enumerate(ts)])
@@ -269,10 +591,13 @@ def run_ours(args, dist):
     torch.cuda.synchronize()
     clocks.start()
     l0 = fsolve.fs_kernel_launches()
+    host_s = 0.0
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record()
+        h0 = time.perf_counter()
         step(u0d)
+        host_s += time.perf_counter() - h0
         ev[k][1].record()
     torch.cuda.synchronize()
     launches = (fsolve.fs_kernel_launches() - l0) // max(1, args.steps)
@@ -304,11 +629,8 @@ def run_ours(args, dist):
     algo = {"column": 2 * spec_bytes, "row_c2r": spec_bytes + N * N * 4, "row_r2c": N * N * 4 + spec_bytes,
             "factor": (M + 1 + N) * 16,
             "batch": len(ts) * (3 * spec_bytes + N * N * 4)}.get(name, 0)
-    peak, peak_src = peaks()
     achieved = algo / avg_s / 1e9 if avg_s > 0 else 0.0
-    traffic = None
-    if name == TRAFFIC_CAPTURE["kernel"] and _csrc_digest() == TRAFFIC_CAPTURE["sources_sha256"]:
-        traffic = TRAFFIC_CAPTURE["bytes"]
+    traffic = _capture_traffic("diffusion_1024", name)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": name,
                 "peak_source": peak_src, "avg_launch_us": round(avg_s * 1e6, 3),
@@ -386,8 +708,14 @@ def run_ours(args, dist):
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "parallelism": f"replicas x{dist.world}"},
         "e2e": e2e, "roofline": roofline, "gpu_launches": int(launches), "clocks": clk,
+        "host_us_per_step": round(1e6 * host_s / args.steps, 1),
         "comparators": comparators,
     }
+    legs = [x for x in args.legs.split(",") if x]
+    if legs:
+        line["legs"] = {}
+        for name in legs:
+            line["legs"][name] = LEG_FNS[name](ctx)
     if not args.no_serving:
         # open-loop serving: 20,000 requests, N log-uniform in [128, 8192],
         # mixed operators with follow-ups, 150 GB budget, arrival rate 0.8 x
@@ -399,6 +727,8 @@ def run_ours(args, dist):
         gpu_out = out.cpu().numpy()
         line["cpu_baseline"] = cpu_baseline(u0, lx, ly, D, times, gpu_out)
         line["rel_l2_vs_oracle_max"] = line["cpu_baseline"].pop("rel_l2_vs_oracle_max", None)
+        for name, acc in leg_accuracy(ctx["checks"]).items():
+            line["legs"][name]["accuracy"] = acc
     fsolve.fs_state_destroy(state)
     fsolve.fs_plan_destroy(plan)
     if dist.rank == 0:

@@ -36,8 +36,11 @@
  *               raised while enqueuing returns FS_ERR_CUDA; asynchronous kernel
  *               faults surface at the caller's next synchronisation.
  *   Precision   FS_F32: float fields, FP32 butterflies with twiddles computed
- *               in FP64 and rounded once; spectral factors combined in
- *               double-float (two-float) arithmetic and rounded once.
+ *               in FP64 and rounded once; Poisson factors evaluated in FP64
+ *               and rounded once (a per-plan table built on the first
+ *               Poisson solve, half a spectrum of floats); the other spectral
+ *               factors combined in double-float (two-float) arithmetic and
+ *               rounded once.
  *               Target: rel-L2 <= 1e-5 against an FP64 reference.
  *               FS_F64: everything in FP64, target rel-L2 <= 1e-12.
  */
@@ -144,6 +147,35 @@ fs_status fs_diffusion_solve(fs_plan plan, const void *u0, double D, double t, v
  * negative (the solution operator is a group).  u may alias u0. */
 fs_status fs_wave_solve(fs_plan plan, const void *u0, const void *v0, double c, double t,
                         void *u, fs_stream stream);
+
+/* ---------------------------------------------------------------- slab passes
+ * The steps of one solve split by slabs, for a grid shared by several GPUs
+ * (Sec. II.D: the 2D DFT is the x transforms of every row followed by the y
+ * transforms of every column, so a slab of rows and a slab of x frequencies
+ * are each transformed locally; the exchange between the two layouts is the
+ * caller's all-to-all).  `plan` is the plan of the WHOLE grid (its nx, ny,
+ * Lx, Ly, dtype and tables); the calls only enqueue work on `stream` and use
+ * the plan's factor tables, like the solves.
+ *   fs_rows_forward: x transforms of `nrows` real rows f [nrows][nx] ->
+ *     half spectrum spec [nx/2+1][nrows] (x-frequency-major: element (a, y)
+ *     at a*nrows + y), unnormalised (Sec. II.D first step, real input packed
+ *     as in the one-shot solves).  1 <= nrows <= ny.
+ *   fs_columns_apply: for the x frequencies a0 .. a0+ncols-1 (0 <= a0,
+ *     a0 + ncols <= nx/2 + 1), spec_cols [ncols][ny] holding their whole
+ *     columns: forward y transform, the operator of `op` times 1/(nx ny)
+ *     (FS_OP_POISSON, FS_OP_DIFFUSION with D, t >= 0, or FS_OP_WAVE with
+ *     c > 0 and zero initial velocity; Sec. III), inverse y transform, in
+ *     place.
+ *   fs_rows_inverse: inverse x transforms (C2R) of spec [nx/2+1][nrows] ->
+ *     real rows u [nrows][nx].
+ * Buffers are device memory of the plan dtype (complex interleaved for the
+ * spectra), owned by the caller.  Errors: FS_ERR_ARG (NULL, bad range, bad
+ * op or parameters), FS_ERR_CUDA, FS_ERR_NOMEM (first Poisson call on an FP32
+ * plan builds its factor table). */
+fs_status fs_rows_forward(fs_plan plan, int nrows, const void *f, void *spec, fs_stream stream);
+fs_status fs_columns_apply(fs_plan plan, int a0, int ncols, int op, double D, double c, double t,
+                           void *spec_cols, fs_stream stream);
+fs_status fs_rows_inverse(fs_plan plan, int nrows, const void *spec, void *u, fs_stream stream);
 
 /* ---------------------------------------------------------------- complex fields
  * The same three solves for complex fields (Sec. II.B: the samples p_jk may

@@ -1,5 +1,6 @@
 // fs_api.cu -- plans, kept states and the one-shot / advance entry points of
 // the C ABI (include/fsolve.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -251,6 +252,48 @@ static bool apply_cfg(fs_plan_s *t, const TuneCfg &c) {
   return true;
 }
 
+// Poisson factors of an FP32 plan, -1/(nx ny |omega|^2) for every element
+// (a, b) of the half spectrum, evaluated in FP64 from the FP64 axis tables
+// and rounded once to float (Eq. SolutionPoisson with the normalisation of
+// the inverse transform); the zero mode gets 0.
+__global__ void k_poisson_table(float *out, const double *wx2d, const double *wy2d, int ncol, int ny,
+                                double scale) {
+  const size_t n = (size_t)ncol * ny;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(i / ny), b = (int)(i - (size_t)a * ny);
+    const double w2 = wx2d[a] + wy2d[b];
+    out[i] = w2 > 0.0 ? (float)(-scale / w2) : 0.0f;
+  }
+}
+
+// The table is on by default; FS_POISSON_TABLE=0 evaluates the factor per
+// element in two-float instead (for comparison).
+static bool poisson_table_enabled() {
+  static const bool on = [] {
+    const char *v = getenv("FS_POISSON_TABLE");
+    return !(v && *v == '0');
+  }();
+  return on;
+}
+
+// Build the plan's Poisson table on first use (stream-ordered).
+static fs_status ensure_pfac(fs_plan p, cudaStream_t s) {
+  if (p->pfac) return FS_OK;
+  const size_t n = (size_t)(p->M + 1) * p->ny;
+  cudaError_t e = alloc_dev(reinterpret_cast<void **>(&p->pfac), n * sizeof(float));
+  if (e != cudaSuccess) {
+    p->pfac = nullptr;
+    return cuda_error(e, "Poisson factor table allocation");
+  }
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+  k_poisson_table<<<blocks, 256, 0, s>>>(p->pfac, p->wx2d, p->wy2d, p->M + 1, p->ny,
+                                           1.0 / ((double)p->nx * (double)p->ny));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "Poisson factor table");
+  return FS_OK;
+}
+
 static fs_status ensure_work_v(fs_plan p) {
   if (p->work_v) return FS_OK;
   cudaError_t e = alloc_dev(&p->work_v, p->spec_bytes);
@@ -442,6 +485,7 @@ fs_status fs_plan_destroy(fs_plan p) {
   cudaFree(p->work_c);
   cudaFree(p->work_cv);
   cudaFree(p->fac);
+  cudaFree(p->pfac);
   delete p;
   return FS_OK;
 }
@@ -573,6 +617,11 @@ fs_status fs_poisson_solve(fs_plan p, const void *f, void *u, fs_stream stream) 
   d.op = OP_POISSON;
   d.in_u = f;
   d.out_u = u;
+  if (p->dtype == FS_F32 && !p->standalone_small && poisson_table_enabled()) {
+    const fs_status st = ensure_pfac(p, reinterpret_cast<cudaStream_t>(stream));
+    if (st != FS_OK) return st;
+    d.pfac = p->pfac;
+  }
   return run(p, d, stream, "fs_poisson_solve");
 }
 
@@ -608,6 +657,95 @@ fs_status fs_wave_solve(fs_plan p, const void *u0, const void *v0, double c, dou
   d.p_c = c;
   d.p_t = t;
   return run(p, d, stream, "fs_wave_solve");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- slab passes
+// The building blocks of a solve split across ranks by slabs (Sec. II.D: the
+// 2D DFT is the x transforms of every row followed by the y transforms of
+// every column, so a slab of rows and a slab of x frequencies are each
+// transformed locally).  See include/fsolve.h.
+template <typename T>
+static cudaError_t slab_rows(const fs_plan_s *p, int nrows, const void *in, void *spec, void *out, bool inverse,
+                             cudaStream_t s) {
+  Desc d = base_desc(p);
+  d.op = OP_FORWARD;
+  d.ny = nrows;
+  d.n_row_units = (nrows + d.rows_per_unit - 1) / d.rows_per_unit;
+  d.in_u = in;
+  d.work_u = spec;
+  d.out_u = out;
+  return inverse ? Launch<T>::c2r(d, 1, s) : Launch<T>::rows(d, 1, s);
+}
+
+template <typename T>
+static cudaError_t slab_cols(const Desc &d, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (d.op == OP_DIFFUSION) e = Launch<T>::factor(d, s);
+  if (e == cudaSuccess) e = Launch<T>::cols(d, s);
+  return e;
+}
+
+extern "C" {
+
+fs_status fs_rows_forward(fs_plan p, int nrows, const void *f, void *spec, fs_stream stream) {
+  if (!p || !f || !spec) return set_error(FS_ERR_ARG, "fs_rows_forward: NULL argument");
+  if (nrows < 1 || nrows > p->ny) return set_error(FS_ERR_ARG, "fs_rows_forward: need 1 <= nrows <= ny");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const cudaError_t e = p->dtype == FS_F64 ? slab_rows<double>(p, nrows, f, spec, nullptr, false, s)
+                                           : slab_rows<float>(p, nrows, f, spec, nullptr, false, s);
+  return e == cudaSuccess ? FS_OK : cuda_error(e, "fs_rows_forward");
+}
+
+fs_status fs_rows_inverse(fs_plan p, int nrows, const void *spec, void *u, fs_stream stream) {
+  if (!p || !spec || !u) return set_error(FS_ERR_ARG, "fs_rows_inverse: NULL argument");
+  if (nrows < 1 || nrows > p->ny) return set_error(FS_ERR_ARG, "fs_rows_inverse: need 1 <= nrows <= ny");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const cudaError_t e = p->dtype == FS_F64 ? slab_rows<double>(p, nrows, nullptr, const_cast<void *>(spec), u, true, s)
+                                           : slab_rows<float>(p, nrows, nullptr, const_cast<void *>(spec), u, true, s);
+  return e == cudaSuccess ? FS_OK : cuda_error(e, "fs_rows_inverse");
+}
+
+fs_status fs_columns_apply(fs_plan p, int a0, int ncols, int op, double D, double c, double t, void *spec_cols,
+                           fs_stream stream) {
+  if (!p || !spec_cols) return set_error(FS_ERR_ARG, "fs_columns_apply: NULL argument");
+  if (a0 < 0 || ncols < 1 || a0 + ncols > p->M + 1)
+    return set_error(FS_ERR_ARG, "fs_columns_apply: columns a0 .. a0+ncols-1 must lie in 0 .. nx/2");
+  Desc d = base_desc(p);
+  if (op == FS_OP_POISSON) {
+    d.op = OP_POISSON;
+  } else if (op == FS_OP_DIFFUSION) {
+    if (!(D >= 0.0) || !(t >= 0.0) || !std::isfinite(D * t))
+      return set_error(FS_ERR_ARG, "fs_columns_apply: need finite D >= 0 and t >= 0");
+    d.op = OP_DIFFUSION;
+    d.p_dt = D * t;
+    d.p_t = t;
+  } else if (op == FS_OP_WAVE) {
+    if (!(c > 0.0) || !std::isfinite(c) || !std::isfinite(t))
+      return set_error(FS_ERR_ARG, "fs_columns_apply: need finite c > 0 and finite t");
+    d.op = OP_WAVE;
+    d.p_c = c;
+    d.p_t = t;
+  } else {
+    return set_error(FS_ERR_ARG, "fs_columns_apply: op must be FS_OP_POISSON, FS_OP_DIFFUSION or FS_OP_WAVE");
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // columns a0 .. a0+ncols-1 become 0 .. ncols-1 of the descriptor: the x
+  // wavenumber tables (8 bytes per entry in both precisions) start at a0
+  d.M = ncols - 1;
+  d.n_col_units = (ncols + d.cols_per_unit - 1) / d.cols_per_unit;
+  d.n_fac_units = (ncols + p->ny + kFactorPerUnit - 1) / kFactorPerUnit;
+  d.wx2 = static_cast<const char *>(p->wx2) + (size_t)a0 * 8;
+  d.wx2d = p->wx2d + a0;
+  d.work_u = spec_cols;
+  if (d.op == OP_POISSON && p->dtype == FS_F32 && poisson_table_enabled()) {
+    const fs_status st = ensure_pfac(p, s);
+    if (st != FS_OK) return st;
+    d.pfac = p->pfac + (size_t)a0 * p->ny;
+  }
+  const cudaError_t e = p->dtype == FS_F64 ? slab_cols<double>(d, s) : slab_cols<float>(d, s);
+  return e == cudaSuccess ? FS_OK : cuda_error(e, "fs_columns_apply");
 }
 
 fs_status fs_poisson_solve_c(fs_plan p, const void *f, void *u, fs_stream stream) {

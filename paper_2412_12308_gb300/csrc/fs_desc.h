@@ -62,6 +62,7 @@ struct Desc {
   const void *wx2, *wy2;      // |omega_x|^2 (a <= M), |omega_y|^2 (b < ny); two-float or double
   const double *wx2d, *wy2d;  // the same in float64 (factor tables)
   void *fac;                  // diffusion per-axis factors: x part [M+1], y part [ny]
+  const float *pfac;          // FP32 Poisson: -1/(nx ny |omega|^2) per element [M+1][ny], FP64-evaluated (or null)
   double p_dt;                // D * t
   double p_d;                 // diffusivity D (source gain of the diffusion advance)
   double p_c;                 // wave speed c

@@ -47,6 +47,7 @@ struct fs_plan_s {
   // device workspace
   void *work_u, *work_v, *fac;
   void *work_c, *work_cv;  // full spectra nx*ny for complex fields (allocated on first use)
+  float *pfac;             // FP32 plans: Poisson factors [M+1][ny] (built on first use)
   size_t spec_bytes;  // (M+1)*ny complex
 };
 

@@ -44,6 +44,11 @@ struct ProfScope {
   }
 };
 
+// Persistent TMA-staged row passes (fs_rows_tma.cu): FP32, power-of-two row
+// transforms of length 512 .. 4096; false / not launched otherwise.
+bool rows_tma_ok(const Desc &d, int nfields, bool c2r);
+cudaError_t rows_tma_launch(const Desc &d, int nfields, bool c2r, cudaStream_t s);
+
 constexpr int kMaxThreads = 512;
 constexpr int kFactorPerUnit = 256;  // factor-table entries per factor unit
 
@@ -325,6 +330,7 @@ struct Launch {
   }
   // forward pass over the real field(s): fields = 1 or 2
   static cudaError_t rows(const Desc &d, int fields, cudaStream_t s) {
+    if (sizeof(T) == 4 && rows_tma_ok(d, fields, false)) return rows_tma_launch(d, fields, false, s);
     PassKernel k = p2_row(d, false);
     if (!k) k = mx_row(d, false);
     if (!k) k = pass_kernels<T>(d.rp_row.e).r2c;
@@ -375,6 +381,7 @@ struct Launch {
     return launch(k, d.n_col_units, col_threads(d), col_smem(d), d, s, PC_COL);
   }
   static cudaError_t c2r(const Desc &d, int fields, cudaStream_t s) {
+    if (sizeof(T) == 4 && rows_tma_ok(d, fields, true)) return rows_tma_launch(d, fields, true, s);
     PassKernel k = p2_row(d, true);
     if (!k) k = mx_row(d, true);
     if (!k) k = pass_kernels<T>(d.rp_row.e).c2r;

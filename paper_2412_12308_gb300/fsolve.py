@@ -77,6 +77,10 @@ _SIGS = {
                                                _vp, _vp, _vp]),
     "fs_diffusion_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "fs_rows_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "fs_columns_apply": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "fs_rows_inverse": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "fs_poisson_solve_c": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "fs_diffusion_solve_c": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_solve_c": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
@@ -177,15 +181,8 @@ def _key(h):
 
 
 def _plan_geom(plan):
-    k = _key(plan)
-    if k is None:
-        return None
-    g = _plans.get(k)
-    if g is None:
-        info = fs_plan_info(plan)
-        g = (info["nx"], info["ny"], info["dtype"])
-        _plans[k] = g
-    return g
+    """(nx, ny, dtype) of a plan this binding created, else None (unchecked)."""
+    return _plans.get(_key(plan))
 
 
 def _owner_geom(h):
@@ -323,6 +320,40 @@ def fs_plan_tiles(plan):
     v = [ctypes.c_int() for _ in range(4)]
     _check(_lib.fs_plan_tiles(plan, *[ctypes.byref(x) for x in v]), "fs_plan_tiles")
     return tuple(x.value for x in v)
+
+
+def _slab(t, n, dtype, cplx, where, name):
+    """Pointer of a slab buffer with n elements of the plan's type (checked
+    like whole fields; raw integers pass unchecked)."""
+    return _field(t, None if dtype is None else (n, 1, dtype), where, name, cplx)
+
+
+def fs_rows_forward(plan, nrows, f, spec, stream=None):
+    """x transforms of nrows real rows f [nrows][nx] -> spec [nx/2+1][nrows] (complex)."""
+    load()
+    g, w = _plan_geom(plan), "fs_rows_forward"
+    nx, dt = (g[0], g[2]) if g else (None, None)
+    _check(_lib.fs_rows_forward(plan, int(nrows), _slab(f, (nx or 0) * nrows, dt, False, w, "f"),
+                                _slab(spec, ((nx or 0) // 2 + 1) * nrows, dt, True, w, "spec"), _stream(stream)), w)
+
+
+def fs_columns_apply(plan, a0, ncols, op, spec_cols, D=0.0, c=0.0, t=0.0, stream=None):
+    """Forward y transform, operator, inverse y transform of the x frequencies
+    a0 .. a0+ncols-1; spec_cols [ncols][ny] (complex), in place."""
+    load()
+    g, w = _plan_geom(plan), "fs_columns_apply"
+    ny, dt = (g[1], g[2]) if g else (None, None)
+    _check(_lib.fs_columns_apply(plan, int(a0), int(ncols), int(op), float(D), float(c), float(t),
+                                 _slab(spec_cols, (ny or 0) * ncols, dt, True, w, "spec_cols"), _stream(stream)), w)
+
+
+def fs_rows_inverse(plan, nrows, spec, u, stream=None):
+    """Inverse x transforms of spec [nx/2+1][nrows] (complex) -> real rows u [nrows][nx]."""
+    load()
+    g, w = _plan_geom(plan), "fs_rows_inverse"
+    nx, dt = (g[0], g[2]) if g else (None, None)
+    _check(_lib.fs_rows_inverse(plan, int(nrows), _slab(spec, ((nx or 0) // 2 + 1) * nrows, dt, True, w, "spec"),
+                                _slab(u, (nx or 0) * nrows, dt, False, w, "u"), _stream(stream)), w)
 
 
 def fs_poisson_solve_c(plan, f, u, stream=None):

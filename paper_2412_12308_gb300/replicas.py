@@ -42,16 +42,26 @@ def my_share(costs, rank, world):
     return shard(costs, world)[rank]
 
 
-def run_batch_share(problems, rank, world, plans, inputs, outputs, stream=None):
-    """Submit this rank's share of `problems` (workloads.Problem list) as one
-    persistent batch on the current GPU; returns the batch ticket and the
-    indices it covers.  `plans[n]`, `inputs[i]`, `outputs[i]` are this
-    rank's plan handles and device tensors."""
+def batch_share_requests(problems, rank, world, plans, inputs, outputs):
+    """This rank's share of `problems` (workloads.Problem list) as a request
+    array for one persistent batch, and the indices it covers.  `plans[n]`,
+    `inputs[i]`, `outputs[i]` are this rank's plan handles and fields (device
+    tensors, or raw device addresses); nothing is launched."""
     from . import fsolve
 
     ops = {"poisson": fsolve.FS_OP_POISSON, "diffusion": fsolve.FS_OP_DIFFUSION, "wave": fsolve.FS_OP_WAVE}
     idx = my_share([problem_cost(p.n) for p in problems], rank, world)
     reqs = [fsolve.fs_request(ops[problems[i].op], plan=plans[problems[i].n], in_u=inputs[i], out_u=outputs[i],
                               D=problems[i].D, c=problems[i].c, t=problems[i].t) for i in idx]
-    ticket = fsolve.fs_batch_submit(reqs, stream) if reqs else 0
+    return (fsolve.fs_request_array(reqs) if reqs else None), idx
+
+
+def run_batch_share(problems, rank, world, plans, inputs, outputs, stream=None):
+    """Submit this rank's share of `problems` as one persistent batch on the
+    current GPU; returns the batch ticket (0 for an empty share) and the
+    indices it covers."""
+    from . import fsolve
+
+    arr, idx = batch_share_requests(problems, rank, world, plans, inputs, outputs)
+    ticket = fsolve.fs_batch_submit(arr, stream) if arr is not None else 0
     return ticket, idx

@@ -88,3 +88,59 @@ def test_two_gloo_ranks_match_single_process():
         merged.update(g["res"])
     for i in (0, 7, 31, 63):
         assert merged[i] == _solve(probs[i])
+
+
+def _assembly_worker(rank, world, port, q):
+    """Each rank assembles the request array of its share through the product
+    code (replicas.batch_share_requests); plans and fields are stand-in
+    handles and addresses, so nothing reaches a GPU."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    probs = wl.batch_mix()
+    plans = {n: 0x1000 + n for n in sorted({p.n for p in probs})}
+    inputs = {i: 0x10_0000_0000 + (i << 24) for i in range(len(probs))}
+    outputs = {i: 0x20_0000_0000 + (i << 24) for i in range(len(probs))}
+    arr, idx = replicas.batch_share_requests(probs, rank, world, plans, inputs, outputs)
+    rows = [(r.op, r.plan, r.in_u, r.out_u, r.D, r.c, r.t, r.keep, r.parent, r.state, r.in_v, r.out_v)
+            for r in arr]
+    gathered = [None] * world
+    dist.all_gather_object(gathered, {"rank": rank, "idx": idx, "rows": rows})
+    if rank == 0:
+        q.put(gathered)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_batch_share_request_assembly_on_gloo_ranks(world):
+    """The 512-problem mix split across gloo ranks: shares are disjoint and
+    cover every problem, each rank's requests carry its problems' operator,
+    parameters, plan and field addresses in share order, and the shares'
+    grid points are balanced to within the largest problem."""
+    from paper_2412_12308_gb300 import fsolve
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_assembly_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    gathered = sorted(q.get(timeout=300), key=lambda g: g["rank"])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    probs = wl.batch_mix()
+    ops = {"poisson": fsolve.FS_OP_POISSON, "diffusion": fsolve.FS_OP_DIFFUSION, "wave": fsolve.FS_OP_WAVE}
+    seen = []
+    for g in gathered:
+        assert g["idx"] == sorted(g["idx"])
+        assert len(g["rows"]) == len(g["idx"])
+        for i, row in zip(g["idx"], g["rows"]):
+            p = probs[i]
+            assert row == (ops[p.op], 0x1000 + p.n, 0x10_0000_0000 + (i << 24), 0x20_0000_0000 + (i << 24),
+                           p.D, p.c, p.t, 0, 0, None, None, None)
+        seen += g["idx"]
+    assert sorted(seen) == list(range(len(probs)))
+    loads = [sum(probs[i].n ** 2 for i in g["idx"]) for g in gathered]
+    assert max(loads) - min(loads) <= max(p.n ** 2 for p in probs)
