@@ -19,6 +19,14 @@ namespace fs {
 
 std::atomic<unsigned long long> g_launches{0};
 
+bool fp64_factors_requested() {
+  static const bool on = [] {
+    const char *v = getenv("FS_FP64_FACTORS");
+    return v && *v && *v != '0';
+  }();
+  return on;
+}
+
 bool tma_enabled() {
   static const bool on = [] {
     const char *v = getenv("FS_NO_TMA");
@@ -193,6 +201,7 @@ Desc base_desc(const fs_plan_s *p) {
   d.work_u = p->work_u;
   d.work_v = p->work_v;
   d.scale = 1.0 / ((double)p->nx * (double)p->ny);
+  d.wy_unit2 = (2.0 * M_PI / p->ly) * (2.0 * M_PI / p->ly);
   return d;
 }
 
@@ -266,12 +275,15 @@ __global__ void k_poisson_table(float *out, const double *wx2d, const double *wy
   }
 }
 
-// The table is on by default; FS_POISSON_TABLE=0 evaluates the factor per
-// element in two-float instead (for comparison).
+// The table is a measured variant, off by default (FS_POISSON_TABLE=1 turns
+// it on): at 4096^2 its extra read of half a spectrum of floats made the
+// column pass slower (88.0 us) than forming the factor per element in
+// two-float (77.9 us), whose ~44-bit value rounds to the same float except in
+// rare double-rounding cases.
 static bool poisson_table_enabled() {
   static const bool on = [] {
     const char *v = getenv("FS_POISSON_TABLE");
-    return !(v && *v == '0');
+    return v && *v && *v != '0';
   }();
   return on;
 }

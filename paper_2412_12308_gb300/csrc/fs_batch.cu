@@ -426,6 +426,7 @@ static size_t finish_descs(BatchPlan *bp, char *arena) {
   size_t smem = 0;
   for (size_t k = 0; k < bp->descs.size(); ++k) {
     Desc &d = bp->descs[k];
+    fill_op_consts(d);
     char *w = arena + bp->ws_off[k];
     const size_t fb = align256((size_t)(d.M + 1 + d.ny) * 8);  // float2 or double per entry
     const size_t sb = align256((size_t)(d.M + 1) * d.ny * 2 * sizeof(T));

@@ -26,7 +26,8 @@ enum Flags : int {
   F_WANT_V = 2,   // wave advance: also produce v = u_t
   F_SOURCE = 4,   // advance: a kept constant-source spectrum st_s is added
   F_COL_TMA = 8,     // batch: column units stage each column group by a bulk copy
-  F_ROW_STAGED = 16  // batch: C2R row units stage each tile by asynchronous copies
+  F_ROW_STAGED = 16, // batch: C2R row units stage each tile by asynchronous copies
+  F_FP64_FACTORS = 32  // FP32 wave operators: factors evaluated per element in FP64 (measured variant)
 };
 
 // Unit kinds of the persistent batch kernel, in dependency order.
@@ -36,6 +37,18 @@ struct RadixPlan {
   int32_t e;         // elements held per thread (the register tile)
   int32_t n;         // number of stages
   int32_t r[8];      // radix of each stage, product = transform length
+};
+
+// Column-independent operator constants of the FP32 path, split on the host
+// from the double fields below into (hi, lo) float pairs, so the kernels do
+// no FP64 arithmetic (GB300 runs FP64 at a small fraction of the FP32 rate).
+struct OpConstF {
+  float ct_hi, ct_lo;  // c * t
+  float sc_hi, sc_lo;  // scale
+  float dd_hi, dd_lo;  // D
+  float cy_hi, cy_lo;  // wy_unit2
+  float c, t, scale;
+  int ready;           // 1 once filled (fill_op_consts)
 };
 
 struct Desc {
@@ -68,6 +81,8 @@ struct Desc {
   double p_c;                 // wave speed c
   double p_t;                 // time t
   double scale;               // 1 / (nx * ny)
+  double wy_unit2;            // (2 pi / Ly)^2: |omega_y(b)|^2 = wy_unit2 * b'^2 (FP32 operators)
+  OpConstF fc;                // the above as float pairs (FP32 kernels)
 };
 
 }  // namespace fs

@@ -100,6 +100,7 @@ struct Kept {
 struct Flight {
   cudaEvent_t ev = nullptr;
   int slot = 0;
+  bool large = false;  // a batch of grids run as standalone passes
   long long ws_off = -1;
   size_t ws_bytes = 0;
   std::vector<Req> reqs;
@@ -138,6 +139,14 @@ std::mutex g_srv_mu;
 size_t spec_bytes_of(const fs_request &r) {
   fs_plan p = r.plan ? r.plan : (r.state ? r.state->plan : nullptr);
   return p ? p->spec_bytes : 0;
+}
+
+// Grids of at least direct_min_points run as standalone pass kernels inside
+// their batch; a follow-up takes its parent's grid (its plan is filled in at
+// enqueue).
+bool is_large(const Server *S, const Req &q) {
+  return S->direct_min_points > 0 && q.r.plan &&
+         (long long)q.r.plan->nx * q.r.plan->ny >= S->direct_min_points;
 }
 
 void harvest_locked(Server *S) {
@@ -204,6 +213,14 @@ bool launch_one_locked(Server *S) {
       break;
     }
   if (slot < 0 || S->queue.empty()) return false;
+  // A batch holds either grids that run as standalone passes (large) or grids
+  // that share the persistent launch (small), never both, so small requests
+  // do not wait on their stream behind a large grid's passes; large batches
+  // take at most all slots but one, so one slot always serves small ones.
+  int large_in_flight = 0;
+  for (const Flight &f : S->flights) large_in_flight += f.large ? 1 : 0;
+  const bool allow_large = large_in_flight < (int)S->streams.size() - 1;
+  int cls = -1;  // class of this batch: decided by its first request
   std::vector<Req> take;
   std::vector<fs_request> reqs;
   std::vector<void *> keeps;
@@ -211,6 +228,11 @@ bool launch_one_locked(Server *S) {
   bool blocked = false;  // an earlier request did not fit: only follow-ups (which free memory) pass it
   for (auto it = S->queue.begin(); it != S->queue.end() && (int)take.size() < S->max_batch;) {
     Req &q = *it;
+    const int qc = is_large(S, q) ? 1 : 0;
+    if ((qc == 1 && !allow_large) || (cls >= 0 && qc != cls)) {
+      ++it;
+      continue;
+    }
     if (blocked && !q.r.parent) {
       ++it;
       continue;
@@ -267,6 +289,7 @@ bool launch_one_locked(Server *S) {
       S->used += q.keep + q.reserve;
     }
     ws += al256(q.ws);
+    cls = qc;
     reqs.push_back(q.r);
     keeps.push_back(q.keep ? (void *)(S->arena.base + koff) : nullptr);
     take.push_back(q);
@@ -275,6 +298,7 @@ bool launch_one_locked(Server *S) {
   if (take.empty()) return false;
   Flight f;
   f.slot = slot;
+  f.large = cls == 1;
   if (ws) {
     f.ws_off = S->arena.alloc(ws);
     if (f.ws_off < 0) {

@@ -138,6 +138,7 @@ extern "C" fs_status fs_poisson_solve_static(int nx, int ny, double lx, double l
   d.wx2 = base + kOffWx;
   d.wy2 = base + kOffWy;
   d.scale = 1.0 / ((double)nx * (double)ny);
+  d.wy_unit2 = (2.0 * M_PI / ly) * (2.0 * M_PI / ly);
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int n_tab = nx + ny + (d.M + 1) + ny;

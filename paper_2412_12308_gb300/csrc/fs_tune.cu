@@ -34,10 +34,15 @@ std::mutex g_mu;
 std::map<Key, Entry> g_cache;
 bool g_env_loaded = false;
 
+// device name, looked up once per device (cudaGetDeviceProperties is slow);
+// called with g_mu held
 std::string gpu_name(int device) {
+  static std::map<int, std::string> names;
+  auto it = names.find(device);
+  if (it != names.end()) return it->second;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return "unknown";
-  return prop.name;
+  return names[device] = prop.name;
 }
 
 // "key": number from a JSON line (false if absent)
