@@ -245,7 +245,7 @@ def _csrc_digest():
 # configuration of the measured set): the one-shot 4096^2 Poisson solve with
 # the plain per-solve comparator, the 4096^2 wave with 50 snapshots from one
 # kept spectrum, and the 512-problem uneven batch (sharded across ranks).
-LEGS = ("poisson_4096", "wave_4096_snapshots", "batch_mix_512")
+LEGS = ("poisson_4096", "wave_4096_snapshots", "batch_mix_512", "factors_4096")
 
 
 def _spec_bytes(n, esz=4):
@@ -497,7 +497,33 @@ def leg_wave_advance_4096(ctx):
     return res
 
 
-LEG_FNS = {"poisson_4096": leg_poisson_4096, "wave_4096_snapshots": leg_wave_4096_snapshots,
+def leg_factors_4096(ctx):
+    """Cost of the spectral factors on a 4096^2 half spectrum (8.4M elements):
+    evaluated as the FP32 column pass does (two-float, hardware sine/cosine
+    of the reduced phase) and in FP64 rounded once (fs_operator_factors, one
+    float written per element, the same bytes both ways)."""
+    torch, fsolve, dev, flush, reps = ctx["torch"], ctx["fsolve"], ctx["dev"], ctx["flush"], ctx["reps"]
+    n = 4096
+    plan = fsolve.fs_plan_create(n, n, 1.0, 1.0, fsolve.FS_F32)
+    out = torch.empty((n // 2 + 1) * n, dtype=torch.float32, device=dev)
+    res = {"workload": "operator factors of every half-spectrum element, 4096x4096 FP32 plan",
+           "elements": (n // 2 + 1) * n}
+    cases = (("poisson", fsolve.FS_OP_POISSON, {}), ("diffusion", fsolve.FS_OP_DIFFUSION, {"D": 0.1, "t": 0.5}),
+             ("wave", fsolve.FS_OP_WAVE, {"c": 1.0, "t": 0.37}))
+    for name, op, kw in cases:
+        row = {}
+        for fp64 in (False, True):
+            def run():
+                fsolve.fs_operator_factors(plan, op, out, fp64=fp64, **kw)
+            run()
+            row["fp64_us" if fp64 else "two_float_us"] = round(1e3 * statistics.mean(_events_ms(torch, run, reps, flush)), 3)
+        res[name] = row
+    fsolve.fs_plan_destroy(plan)
+    return res
+
+
+LEG_FNS = {"factors_4096": leg_factors_4096, "poisson_4096": leg_poisson_4096,
+           "wave_4096_snapshots": leg_wave_4096_snapshots,
            "batch_mix_512": leg_batch_mix_512, "wave_advance_4096": leg_wave_advance_4096}
 
 

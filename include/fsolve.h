@@ -177,6 +177,21 @@ fs_status fs_columns_apply(fs_plan plan, int a0, int ncols, int op, double D, do
                            void *spec_cols, fs_stream stream);
 fs_status fs_rows_inverse(fs_plan plan, int nrows, const void *spec, void *u, fs_stream stream);
 
+/* ---------------------------------------------------------------- operator factors
+ * fs_operator_factors: the real multiplier the FP32 column pass applies to
+ * every half-spectrum element (a, b) of `plan`'s grid (Sec. III: Poisson
+ * -1/|omega|^2, diffusion exp(-D |omega|^2 t), wave cos(c |omega| t) -- the
+ * factor of U0 --, each times 1/(nx ny)), written to out [nx/2+1][ny]
+ * (float, x-frequency-major, device memory owned by the caller).
+ * fp64 = 0: evaluated exactly as the column pass does (two-float, hardware
+ * sine/cosine of the reduced phase); fp64 = 1: evaluated in FP64 and rounded
+ * once.  For measuring the FP32 path's factor precision and the cost of FP64
+ * evaluation; the solves never call it.  FP32 plans only; op is
+ * FS_OP_POISSON, FS_OP_DIFFUSION (D, t >= 0) or FS_OP_WAVE (c > 0).
+ * Errors: FS_ERR_ARG, FS_ERR_CUDA. */
+fs_status fs_operator_factors(fs_plan plan, int op, double D, double c, double t, int fp64, void *out,
+                              fs_stream stream);
+
 /* ---------------------------------------------------------------- complex fields
  * The same three solves for complex fields (Sec. II.B: the samples p_jk may
  * be complex; the full spectrum is used, a = 0..nx-1).  Fields are

@@ -19,14 +19,6 @@ namespace fs {
 
 std::atomic<unsigned long long> g_launches{0};
 
-bool fp64_factors_requested() {
-  static const bool on = [] {
-    const char *v = getenv("FS_FP64_FACTORS");
-    return v && *v && *v != '0';
-  }();
-  return on;
-}
-
 bool tma_enabled() {
   static const bool on = [] {
     const char *v = getenv("FS_NO_TMA");
@@ -215,6 +207,17 @@ static double omega2_axis(int a, int n, double len) {
   const int ap = (2 * a <= n) ? a : a - n;
   const double w = 2.0 * M_PI * (double)ap / len;
   return w * w;
+}
+
+// The FP32 wave operators reduce the phase c |omega| t modulo 2 pi in
+// two-float (~44 bits), so the phase keeps ~2^-44 |theta| absolute accuracy;
+// beyond |theta| = 2^20 that would grow past the hardware sine/cosine's own
+// error (2^-21.4), so FP32 plans reject larger phases.  FP64 plans evaluate
+// the phase in double.
+bool wave_phase_ok(const fs_plan_s *p, double c, double t) {
+  if (p->dtype == FS_F64) return true;
+  const double wx = M_PI * p->nx / p->lx, wy = M_PI * p->ny / p->ly;  // largest |omega_x|, |omega_y|
+  return std::fabs(c * t) * std::sqrt(wx * wx + wy * wy) <= 1048576.0;
 }
 
 }  // namespace fs
@@ -656,6 +659,8 @@ fs_status fs_wave_solve(fs_plan p, const void *u0, const void *v0, double c, dou
   if (!p || !u0 || !u) return set_error(FS_ERR_ARG, "fs_wave_solve: NULL argument");
   if (!(c > 0.0) || !std::isfinite(c) || !std::isfinite(t))
     return set_error(FS_ERR_ARG, "fs_wave_solve: need finite c > 0 and finite t");
+  if (!wave_phase_ok(p, c, t))
+    return set_error(FS_ERR_ARG, "fs_wave_solve: wave phase out of range (FP32 plans need c |t| |omega|_max <= 2^20)");
   if (v0 && !p->standalone_small) {
     fs_status st = ensure_work_v(p);
     if (st != FS_OK) return st;
@@ -669,6 +674,91 @@ fs_status fs_wave_solve(fs_plan p, const void *u0, const void *v0, double c, dou
   d.p_c = c;
   d.p_t = t;
   return run(p, d, stream, "fs_wave_solve");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- operator factors
+// The real multiplier the FP32 column pass applies to each half-spectrum
+// element (a, b) (for the wave: the factor of U0, cos(c|w|t) / (nx ny)),
+// evaluated as the column pass does (two-float, fs_ops.cuh) or in FP64 and
+// rounded once; a measurement of the FP32 path's factor precision and of
+// the cost of FP64 evaluation on this GPU.
+template <bool FP64>
+__global__ void k_op_factors(const Desc d, float *out) {
+  const size_t n = (size_t)(d.M + 1) * d.ny;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(i / d.ny), b = (int)(i - (size_t)a * d.ny);
+    if constexpr (FP64) {
+      const int bp = (2 * b <= d.ny) ? b : b - d.ny;
+      const double w2 = d.wx2d[a] + d.wy_unit2 * ((double)bp * (double)bp);
+      double f;
+      if (d.op == OP_POISSON) {
+        f = w2 > 0.0 ? -d.scale / w2 : 0.0;
+      } else if (d.op == OP_DIFFUSION) {
+        f = d.scale * exp(-d.p_dt * w2);
+      } else {
+        f = d.scale * cos(d.p_c * d.p_t * sqrt(w2));
+      }
+      out[i] = (float)f;
+    } else {
+      const OpCtx<float> o = op_ctx<float>(d, a);
+      float f;
+      if (d.op == OP_POISSON) {
+        f = poisson_mult(o, d, b);
+      } else if (d.op == OP_DIFFUSION) {
+        f = diff_mult(o, d, b);
+      } else {
+        f = wave_mult(o, d, b).cu;
+      }
+      out[i] = f;
+    }
+  }
+}
+
+extern "C" {
+
+fs_status fs_operator_factors(fs_plan p, int op, double D, double c, double t, int fp64, void *out,
+                              fs_stream stream) {
+  if (!p || !out) return set_error(FS_ERR_ARG, "fs_operator_factors: NULL argument");
+  if (p->dtype != FS_F32) return set_error(FS_ERR_ARG, "fs_operator_factors: FP32 plans only");
+  Desc d = base_desc(p);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (op == FS_OP_POISSON) {
+    d.op = OP_POISSON;
+  } else if (op == FS_OP_DIFFUSION) {
+    if (!(D >= 0.0) || !(t >= 0.0) || !std::isfinite(D * t))
+      return set_error(FS_ERR_ARG, "fs_operator_factors: need finite D >= 0 and t >= 0");
+    d.op = OP_DIFFUSION;
+    d.p_dt = D * t;
+    d.p_t = t;
+  } else if (op == FS_OP_WAVE) {
+    if (!(c > 0.0) || !std::isfinite(c) || !std::isfinite(t))
+      return set_error(FS_ERR_ARG, "fs_operator_factors: need finite c > 0 and finite t");
+    if (!wave_phase_ok(p, c, t))
+      return set_error(FS_ERR_ARG,
+                       "fs_operator_factors: wave phase out of range (FP32 plans need c |t| |omega|_max <= 2^20)");
+    d.op = OP_WAVE;
+    d.p_c = c;
+    d.p_t = t;
+  } else {
+    return set_error(FS_ERR_ARG, "fs_operator_factors: op must be FS_OP_POISSON, FS_OP_DIFFUSION or FS_OP_WAVE");
+  }
+  fill_op_consts(d);
+  cudaError_t e = cudaSuccess;
+  if (d.op == OP_DIFFUSION && !fp64) e = Launch<float>::factor(d, s);
+  if (e == cudaSuccess) {
+    const size_t n = (size_t)(p->M + 1) * p->ny;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+    ProfScope ps(PC_FACTOR, s);
+    if (fp64)
+      k_op_factors<true><<<blocks, 256, 0, s>>>(d, reinterpret_cast<float *>(out));
+    else
+      k_op_factors<false><<<blocks, 256, 0, s>>>(d, reinterpret_cast<float *>(out));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? FS_OK : cuda_error(e, "fs_operator_factors");
 }
 
 }  // extern "C"
@@ -736,6 +826,9 @@ fs_status fs_columns_apply(fs_plan p, int a0, int ncols, int op, double D, doubl
   } else if (op == FS_OP_WAVE) {
     if (!(c > 0.0) || !std::isfinite(c) || !std::isfinite(t))
       return set_error(FS_ERR_ARG, "fs_columns_apply: need finite c > 0 and finite t");
+    if (!wave_phase_ok(p, c, t))
+      return set_error(FS_ERR_ARG,
+                       "fs_columns_apply: wave phase out of range (FP32 plans need c |t| |omega|_max <= 2^20)");
     d.op = OP_WAVE;
     d.p_c = c;
     d.p_t = t;
@@ -788,6 +881,8 @@ fs_status fs_wave_solve_c(fs_plan p, const void *u0, const void *v0, double c, d
   if (!p || !u0 || !u) return set_error(FS_ERR_ARG, "fs_wave_solve_c: NULL argument");
   if (!(c > 0.0) || !std::isfinite(c) || !std::isfinite(t))
     return set_error(FS_ERR_ARG, "fs_wave_solve_c: need finite c > 0 and finite t");
+  if (!wave_phase_ok(p, c, t))
+    return set_error(FS_ERR_ARG, "fs_wave_solve_c: wave phase out of range (FP32 plans need c |t| |omega|_max <= 2^20)");
   Desc d = complex_desc(p);
   d.op = OP_WAVE;
   d.flags = v0 ? F_HAS_V0 : 0;
@@ -990,6 +1085,8 @@ fs_status fs_wave_advance(fs_state s, double c, double t, void *u_out, void *v_o
   if (!s || !u_out) return set_error(FS_ERR_ARG, "fs_wave_advance: NULL argument");
   if (!(c > 0.0) || !std::isfinite(c) || !std::isfinite(t))
     return set_error(FS_ERR_ARG, "fs_wave_advance: need finite c > 0 and finite t");
+  if (!wave_phase_ok(s->plan, c, t))
+    return set_error(FS_ERR_ARG, "fs_wave_advance: wave phase out of range (FP32 plans need c |t| |omega|_max <= 2^20)");
   fs_plan p = s->plan;
   if (v_out && !p->standalone_small) {
     fs_status st = ensure_work_v(p);

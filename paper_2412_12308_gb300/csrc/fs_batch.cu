@@ -159,6 +159,8 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
       case FS_OP_WAVE_ADVANCE:
         if (!(r.c > 0.0) || !std::isfinite(r.c) || !std::isfinite(r.t))
           return set_error(FS_ERR_ARG, "fs_batch_submit: wave needs finite c > 0 and t");
+        if (!wave_phase_ok(p, r.c, r.t))
+          return set_error(FS_ERR_ARG, "fs_batch_submit: wave phase out of range (FP32: c |t| |omega|_max <= 2^20)");
         d.p_c = r.c;
         d.p_t = r.t;
         if (r.op == FS_OP_WAVE) {

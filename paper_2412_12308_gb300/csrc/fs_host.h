@@ -83,4 +83,7 @@ Desc base_desc(const fs_plan_s *p);
 fs_status forward_into(const fs_plan_s *p, const void *u0, const void *v0, void *su, void *sv,
                        fs_stream stream, const char *what);
 size_t fac_bytes(const fs_plan_s *p);
+// FP32 plans: the wave phase c |t| |omega|_max stays within 2^20 (the range
+// in which the two-float phase reduction keeps its accuracy); FP64: always.
+bool wave_phase_ok(const fs_plan_s *p, double c, double t);
 }  // namespace fs

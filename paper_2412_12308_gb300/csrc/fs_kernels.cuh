@@ -47,7 +47,6 @@ struct ProfScope {
 // Persistent TMA-staged row passes (fs_rows_tma.cu): FP32, power-of-two row
 // transforms of length 512 .. 4096; false / not launched otherwise.
 bool rows_tma_ok(const Desc &d, int nfields, bool c2r);
-bool fp64_factors_requested();  // env FS_FP64_FACTORS=1
 cudaError_t rows_tma_launch(const Desc &d, int nfields, bool c2r, cudaStream_t s);
 
 constexpr int kMaxThreads = 512;
@@ -340,11 +339,6 @@ struct Launch {
   static cudaError_t cols(const Desc &d_in, cudaStream_t s) {
     Desc d = d_in;
     fill_op_consts(d);
-    // measured variant: FP32 wave factors evaluated per element in FP64
-    // (FS_FP64_FACTORS=1; standalone column passes of plans with FP64 tables)
-    if (sizeof(T) == 4 && fp64_factors_requested() && d.wx2d &&
-        (d.op == OP_WAVE || d.op == OP_WAVE_ADV) && !(d.flags & F_SOURCE))
-      d.flags |= F_FP64_FACTORS;
     // advances with a constant source: their own instantiations
     if (d.flags & F_SOURCE) {
       PassKernel k = nullptr;

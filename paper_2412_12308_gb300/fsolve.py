@@ -77,6 +77,8 @@ _SIGS = {
                                                _vp, _vp, _vp]),
     "fs_diffusion_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fs_wave_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "fs_operator_factors": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, _vp, _vp]),
     "fs_rows_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "fs_columns_apply": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, _vp, _vp]),
@@ -326,6 +328,16 @@ def _slab(t, n, dtype, cplx, where, name):
     """Pointer of a slab buffer with n elements of the plan's type (checked
     like whole fields; raw integers pass unchecked)."""
     return _field(t, None if dtype is None else (n, 1, dtype), where, name, cplx)
+
+
+def fs_operator_factors(plan, op, out, D=0.0, c=0.0, t=0.0, fp64=False, stream=None):
+    """The FP32 column pass's multiplier for every half-spectrum element into
+    out [nx/2+1][ny] (float32); fp64=True evaluates it in FP64 instead."""
+    load()
+    g, w = _plan_geom(plan), "fs_operator_factors"
+    n = (g[0] // 2 + 1) * g[1] if g else 0
+    _check(_lib.fs_operator_factors(plan, int(op), float(D), float(c), float(t), 1 if fp64 else 0,
+                                    _slab(out, n, g[2] if g else None, False, w, "out"), _stream(stream)), w)
 
 
 def fs_rows_forward(plan, nrows, f, spec, stream=None):

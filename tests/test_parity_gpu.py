@@ -199,6 +199,15 @@ def test_rejections_on_device(gpu_lib):
             gpu_lib.fs_wave_solve(p.h, x, None, 0.0, 1.0, x)
         with pytest.raises(fsolve.FsError):
             gpu_lib.fs_poisson_solve(p.h, None, x)
+        # FP32 wave phases beyond 2^20 (c |t| |omega|_max) are refused: the
+        # two-float phase reduction would lose accuracy past that range
+        with pytest.raises(fsolve.FsError) as ei:
+            gpu_lib.fs_wave_solve(p.h, x, None, 1.0, 1.0e5, x)
+        assert "phase" in str(ei.value)
+        gpu_lib.fs_wave_solve(p.h, x, None, 1.0, 1000.0, x)  # 1000 * pi * 64 * sqrt(2) < 2^20
+    with Plan(gpu_lib, 64, 64, 1.0, 1.0, 1) as p:  # FP64 plans take any phase
+        x = p.dev(np.zeros((64, 64)))
+        gpu_lib.fs_wave_solve(p.h, x, None, 1.0, 1.0e5, x)
 
 
 @pytest.mark.parametrize("nx,ny", [(2048, 2048), (4096, 4096), (8192, 8192), (1536, 1536), (2560, 2560),
