@@ -641,11 +641,11 @@ using namespace fs;
 extern "C" fs_status fs_batch_submit(const fs_request *reqs, int n, uint64_t *ticket_out, fs_stream stream) {
   if (ticket_out) *ticket_out = 0;
   if (!reqs || n <= 0) return set_error(FS_ERR_ARG, "fs_batch_submit: empty batch");
-  // grids of more than 4096^2 points fill the GPU on their own: they run as
-  // the standalone pass kernels, in order, before the persistent launch.
-  // 4096^2 itself runs faster as staged units (measured on GB300, 100
-  // diffusion advances: 10.91 ms as passes, 8.91 ms as units)
-  const long long direct_min = env_ll("FS_BATCH_DIRECT_MIN", 4096LL * 4096LL + 1);
+  // grids of 4096^2 points and more fill the GPU on their own: they run as
+  // the standalone pass kernels (persistent TMA row passes, staged column
+  // pass), in order, before the persistent launch (measured on GB300, 50
+  // wave advances of 4096^2: 11.5k/s as passes, 10.0k/s as batch units)
+  const long long direct_min = env_ll("FS_BATCH_DIRECT_MIN", 4096LL * 4096LL);
   return batch_submit_internal(reqs, n, nullptr, ticket_out, reinterpret_cast<cudaStream_t>(stream), nullptr, 0,
                                direct_min);
 }

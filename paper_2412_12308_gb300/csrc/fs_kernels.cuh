@@ -116,6 +116,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // THREADS = 512 (one CTA per SM at 128 registers) or 256 (two CTAs per SM:
 // one unit's barrier waits overlap the other's work); the batch plan picks 256
 // when every problem's transforms fit and shapes its tiles accordingly.
+
 template <typename T, int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : (THREADS == 256 ? 2 : 1)) k_batch(const Desc *__restrict__ descs,
                                                        const int4 *__restrict__ units, int n_units,

@@ -316,6 +316,7 @@ bool spec_map(CUtensorMap *tm, void *spec, int ny, int M, int R) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+
 template <int M, int R_>
 cudaError_t launch_m(const Desc &d, int nfields, bool c2r, cudaStream_t s) {
   using C = RT<M, R_>;

@@ -295,3 +295,4 @@ def test_staged_units_bit_identical_to_unstaged(gpu_lib, tmp_path, monkeypatch):
     for i, o in enumerate(got):
         assert np.isfinite(o).all(), i
         assert np.array_equal(o, ref[f"arr_{i}"]), (i, STAGED_SHAPES[i // 7])
+
