@@ -223,7 +223,18 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 # for the CUDA sources they were taken on: any change to the sources makes the
 # reported traffic null until a new capture.
 # (workload, kernel class) -> {"bytes": DRAM bytes per launch, "sources_sha256": digest of csrc/}
-TRAFFIC_CAPTURES = {}
+_SRC = "0a7ebacb8d90f93cf4ac3f209582f80951020093e3db62b2f90ea7fa0a6df763"
+TRAFFIC_CAPTURES = {
+    # profiles/k_batch_diffusion_1024.md
+    ("diffusion_1024", "batch"): {"bytes": 169_899_264 + 785_318_144, "sources_sha256": _SRC},
+    # profiles/poisson_4096_pass_kernels.md
+    ("poisson_4096", "row_r2c"): {"bytes": 67_157_760 + 21_002_752, "sources_sha256": _SRC},
+    ("poisson_4096", "column"): {"bytes": 67_234_816 + 7_008_768, "sources_sha256": _SRC},
+    ("poisson_4096", "row_c2r"): {"bytes": 67_192_832 + 17_466_880, "sources_sha256": _SRC},
+    # profiles/wave_4096_snapshots_and_batch_mix_traffic.md
+    ("wave_4096_snapshots", "column"): {"bytes": 67_221_248 + 7_789_568, "sources_sha256": _SRC},
+    ("batch_mix_512", "batch"): {"bytes": 3_932_552_704 + 4_320_621_568, "sources_sha256": _SRC},
+}
 
 
 def _csrc_digest():
@@ -327,6 +338,8 @@ def leg_poisson_4096(ctx):
     passes = {"row_r2c": real + spec, "column": 2 * spec, "row_c2r": spec + real}
     per_pass = {k: {"us": round(kus[k][1], 3), "algorithmic_GBps": round(b / (kus[k][1] * 1e-6) / 1e9, 1),
                     "traffic": _capture_traffic("poisson_4096", k)} for k, b in passes.items() if k in kus}
+    tr = [v["traffic"] for v in per_pass.values()]
+    solve_traffic = sum(tr) if len(tr) == 3 and all(x is not None for x in tr) else None
     # plain path on the same GPU
     kx = 2 * math.pi * torch.fft.rfftfreq(n, d=1.0 / n, device=dev).double()
     ky = 2 * math.pi * torch.fft.fftfreq(n, d=1.0 / n, device=dev).double()
@@ -346,7 +359,7 @@ def leg_poisson_4096(ctx):
         "workload": "Poisson, periodic [0,1)^2, 4096x4096 FP32, 8-mode source |k|<=40, one solve per call",
         "value": round(1e3 / ms_solve, 2), "unit": "solves/s", "ms_per_solve": round(ms_solve, 5),
         "gpu_launches_per_solve": int(launches),
-        "roofline": _roof(24 * n * n, ms_solve * 1e-3, ctx["peak"], ctx["peak_src"],
+        "roofline": _roof(24 * n * n, ms_solve * 1e-3, ctx["peak"], ctx["peak_src"], solve_traffic,
                           what="24N^2 algorithmic bytes (3 passes) per solve / solve time", passes=per_pass),
         "plain_torch_fft": {"value": round(1e3 / ms_plain, 2), "unit": "solves/s", "ms_per_solve": round(ms_plain, 5),
                             "what": "torch.fft.rfft2 -> FP32 multiply by -1/|k|^2 -> irfft2 (cuFFT)"},

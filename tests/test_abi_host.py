@@ -107,6 +107,10 @@ def test_null_handles_are_rejected(lib):
     assert lib.fs_poisson_solve_c(None, None, None, None) == -1
     assert lib.fs_state_load(None, None, 0, None) == -1
     assert lib.fs_state_save(None, None, 0, None) == -1
+    assert lib.fs_rows_forward(None, 4, None, None, None) == -1
+    assert lib.fs_rows_inverse(None, 4, None, None, None) == -1
+    assert lib.fs_columns_apply(None, 0, 1, 0, 0.0, 0.0, 0.0, None, None) == -1
+    assert lib.fs_operator_factors(None, 0, 0.0, 0.0, 0.0, 0, None, None) == -1
 
 
 def test_binding_raises_with_message(lib):
