@@ -2,8 +2,9 @@
 
 The variant replaces the first radix-16 stage of the inverse column
 transform in advances by a tensor-core matmul with three-term BF16 operands.
-It must stay within the FP32 bar against the float64 oracle (rel-L2 <= 1e-5),
-and it must actually run (its rounding differs from the FP32 path's).
+It must stay within the FP32 bar against the float64 oracle (rel-L2 <= 1e-5)
+on the 4096^2 wave snapshots the FP32 path is checked on, and it must
+actually run (its rounding differs from the FP32 path's).
 """
 
 import numpy as np
@@ -58,7 +59,8 @@ def test_tc_variant_wave_4096(gpu_lib, monkeypatch):
     try:
         fd = torch.tensor(u0, dtype=torch.float32, device="cuda")
         F = oracle.state_spectrum(u0)
-        for t in (float(times[24]), float(times[-1])):
+        # every 10th of the 50 snapshots (t = 0.2, 0.4, ..., 1), as for the FP32 path
+        for t in [float(times[j]) for j in range(9, len(times), 10)]:
             U, _ = oracle.wave_spectrum(F, None, c, t, lx, ly)
             want = np.real(oracle.idft2(U))
             got = _advance(plan, fd, c, t, True, monkeypatch)
