@@ -46,6 +46,8 @@ struct Slot {
   int device = -1;
   cudaEvent_t ev = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t cap2 = nullptr;                       // the small problems' branch of the graph
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // capture-time fork / join of that branch
   uint64_t ticket = 0;
   bool pending = false;
   Desc *d_descs = nullptr;
@@ -56,13 +58,18 @@ struct Slot {
   size_t cap_descs = 0, cap_units = 0, cap_arena = 0;
   Desc *h_descs = nullptr;
   int4 *h_units = nullptr;
-  int *h_status = nullptr;
+  int *h_status = nullptr;  // ctl words of the two launches: [1] and [3] are their status
   cudaGraphExec_t gexec = nullptr;
   int key_descs = -1, key_units = -1, key_grid = -1, key_dtype = -1;
   size_t key_smem = 0;
   unsigned long long key_wait = 0;
   int key_threads = 0;
+  int key_small_units = 0, key_small_grid = 0, key_small_threads = 0;
+  size_t key_small_smem = 0;
 };
+
+// status of a slot's last batch: the first non-zero of its two launches
+int slot_status(const Slot *s) { return s->h_status[1] != 0 ? s->h_status[1] : s->h_status[3]; }
 
 std::mutex g_mu;
 std::vector<Slot *> g_slots;
@@ -247,12 +254,24 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
   // 256: 1024^2 504 -> 477 us, 512^2 149 -> 140 us, 2048^2 2006 -> 1950 us,
   // 256^2 60 -> 63 us.  Tile shapes follow; a row's or column's arithmetic
   // does not depend on how many share a CTA.
+  // Single-CTA small problems in a batch that also has work units run as a
+  // second launch beside the persistent one (their half spectrum in shared
+  // memory would otherwise set every CTA's shared memory and size, one CTA
+  // of 512 threads per SM; measured on GB300, 512-problem mix: 6.82 ms with
+  // them inside, 5.34 ms for the same batch without them).
+  bool any_small = false, any_units = false;
+  for (int k = 0; k < n; ++k) {
+    if (bp->direct[k]) continue;
+    (bp->descs[k].small ? any_small : any_units) = true;
+  }
+  const bool split_small = any_small && any_units;
   {
     int need = 1;
     bool p2_large = true;
     for (int k = 0; k < n; ++k) {
       if (bp->direct[k]) continue;
       const Desc &d = bp->descs[k];
+      if (d.small && split_small) continue;
       need = std::max(need, std::max(d.M / d.rp_row.e, d.ny / d.rp_col.e));
       if (d.small) need = kMaxThreads;
       p2_large = p2_large && bp->dtype == FS_F32 && d.rp_row.e == 16 && d.rp_col.e == 16 && p2_row_ok(d.M) &&
@@ -262,7 +281,7 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
     if (const char *v = getenv("FS_BATCH_THREADS")) {
       int maxe = 1;  // the override may force 256 when every transform fits
       for (int k = 0; k < n; ++k)
-        if (!bp->direct[k])
+        if (!bp->direct[k] && !(bp->descs[k].small && split_small))
           maxe = std::max(maxe, std::max(bp->descs[k].M / bp->descs[k].rp_row.e, bp->descs[k].ny / bp->descs[k].rp_col.e));
       if (atoi(v) == 512 || (atoi(v) == 256 && maxe <= 256) || (atoi(v) == 128 && maxe <= 128))
         bp->threads = atoi(v);
@@ -297,8 +316,9 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
         d.flags |= F_ROW_STAGED;
       d.n_col_units = (d.M + 1 + cc - 1) / cc;
       if (d.small) {
-        if (d.small_rows * tr > bp->threads) d.small_rows = std::max(1, bp->threads / tr);
-        if (d.small_cols * tseg > bp->threads) d.small_cols = std::max(1, bp->threads / tseg);
+        const int st = split_small ? bp->small_threads : bp->threads;
+        if (d.small_rows * tr > st) d.small_rows = std::max(1, st / tr);
+        if (d.small_cols * tseg > st) d.small_cols = std::max(1, st / tseg);
       }
     }
   }
@@ -352,7 +372,7 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
       const Desc &d = bp->descs[k];
       if (bp->direct[k]) continue;
       if (d.small) {
-        bp->units.push_back(make_int4(k, K_SMALL, 0, 0));
+        if (!split_small) bp->units.push_back(make_int4(k, K_SMALL, 0, 0));
         continue;
       }
       if (d.op == OP_DIFFUSION || d.op == OP_DIFF_ADV)
@@ -385,6 +405,13 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
     if (i - 1 >= 0 && i - 1 < nch) emit_col(i - 1);
     if (i - 2 >= 0 && i - 2 < nch) emit_c2r(i - 2);
   }
+  // the second launch's table: small problems, largest first
+  if (split_small)
+    for (int k = 0; k < n; ++k)
+      if (bp->descs[k].small && !bp->direct[k]) {
+        bp->units.push_back(make_int4(k, K_SMALL, 0, 0));
+        ++bp->n_small_units;
+      }
   return FS_OK;
 }
 
@@ -426,6 +453,7 @@ static cudaError_t run_direct(const Desc &d0, cudaStream_t s) {
 template <typename T>
 static size_t finish_descs(BatchPlan *bp, char *arena) {
   size_t smem = 0;
+  bp->small_smem = 0;
   for (size_t k = 0; k < bp->descs.size(); ++k) {
     Desc &d = bp->descs[k];
     fill_op_consts(d);
@@ -443,7 +471,11 @@ static size_t finish_descs(BatchPlan *bp, char *arena) {
                           (d.op == OP_WAVE_ADV && (d.flags & F_WANT_V));
       if (need_v) d.work_v = w;
     }
-    if (!bp->direct[k]) smem = std::max(smem, unit_smem<T>(d));
+    if (bp->direct[k]) continue;
+    if (d.small && bp->n_small_units > 0)
+      bp->small_smem = std::max(bp->small_smem, unit_smem<T>(d));
+    else
+      smem = std::max(smem, unit_smem<T>(d));
   }
   return smem;
 }
@@ -488,7 +520,7 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
       }
       if (q != cudaSuccess) return cuda_error(q, "fs_batch_submit: event query");
       c->pending = false;
-      remember(c->ticket, c->h_status[1]);
+      remember(c->ticket, slot_status(c));
     }
     s = c;
     break;
@@ -497,7 +529,7 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
     e = cudaEventSynchronize(oldest->ev);
     if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: wait for a slot");
     oldest->pending = false;
-    remember(oldest->ticket, oldest->h_status[1]);
+    remember(oldest->ticket, slot_status(oldest));
     s = oldest;
   }
   if (!s) {
@@ -505,8 +537,11 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
     s->device = dev;
     e = cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_status, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_ctl, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_status, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_ctl, 4 * sizeof(int));
     if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: slot creation");
     g_slots.push_back(s);
   }
@@ -536,7 +571,8 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
   const int dtype = bp.dtype;
   char *arena = ext_arena ? ext_arena : s->d_arena;
   const size_t smem = dtype == FS_F64 ? finish_descs<double>(&bp, arena) : finish_descs<float>(&bp, arena);
-  if (smem > kMaxDynSmem) return set_error(FS_ERR_SIZE, "fs_batch_submit: unit shared memory too large");
+  if (smem > kMaxDynSmem || bp.small_smem > kMaxDynSmem)
+    return set_error(FS_ERR_SIZE, "fs_batch_submit: unit shared memory too large");
   if (inject) {
     // test hook: make the first three-pass problem's column units wait for a
     // row tile that is never produced, so the bounded wait expires
@@ -555,7 +591,7 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
     if (e != cudaSuccess) return cuda_error(e, "batch: standalone pass launch");
   }
   if (nu == 0) {
-    s->h_status[0] = s->h_status[1] = 0;
+    s->h_status[0] = s->h_status[1] = s->h_status[2] = s->h_status[3] = 0;
     e = cudaEventRecord(s->ev, stream);
     if (e != cudaSuccess) return cuda_error(e, "batch: event record");
     s->pending = true;
@@ -566,28 +602,39 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
   memcpy(s->h_descs, bp.descs.data(), nd * sizeof(Desc));
   memcpy(s->h_units, bp.units.data(), nu * sizeof(int4));
 
+  // the persistent launch over the table's first nm units and, when the
+  // batch has both kinds, the small problems' launch over the last ns
+  const int ns = bp.n_small_units, nm = (int)nu - ns;
   int per_sm = 0, sms = 0;
   int threads = bp.threads;
-  auto occupancy = [&](int th) {
-    return dtype == FS_F64 ? Launch<double>::batch_occupancy(th, smem, &per_sm)
-                           : Launch<float>::batch_occupancy(th, smem, &per_sm);
+  auto occupancy = [&](int th, size_t bytes, int *out) {
+    return dtype == FS_F64 ? Launch<double>::batch_occupancy(th, bytes, out)
+                           : Launch<float>::batch_occupancy(th, bytes, out);
   };
-  e = occupancy(threads);
+  e = occupancy(threads, smem, &per_sm);
   // 256-thread CTAs only pay when two fit on an SM (a resident small problem's
   // half spectrum can take most of the shared memory); the tiles also fit 512
   if (e == cudaSuccess && threads <= 256 && per_sm < 2) {
     threads = kMaxThreads;
-    e = occupancy(threads);
+    e = occupancy(threads, smem, &per_sm);
   }
+  int per_sm2 = 0;
+  const int threads2 = bp.small_threads;
+  const size_t smem2 = bp.small_smem;
+  if (e == cudaSuccess && ns > 0) e = occupancy(threads2, smem2, &per_sm2);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_error(e, "fs_batch_submit: occupancy");
-  if (per_sm < 1) return set_error(FS_ERR_SIZE, "fs_batch_submit: batch kernel does not fit on an SM");
+  if (per_sm < 1 || (ns > 0 && per_sm2 < 1))
+    return set_error(FS_ERR_SIZE, "fs_batch_submit: batch kernel does not fit on an SM");
   int grid = sms * per_sm;
-  if ((size_t)grid > nu) grid = (int)nu;
+  if (grid > nm) grid = nm;
+  int grid2 = ns > 0 ? sms * per_sm2 : 0;
+  if (grid2 > ns) grid2 = ns;
 
   const bool same = s->gexec && s->key_descs == (int)nd && s->key_units == (int)nu && s->key_grid == grid &&
                     s->key_dtype == dtype && s->key_smem == smem && s->key_wait == wait_ns &&
-                    s->key_threads == threads;
+                    s->key_threads == threads && s->key_small_units == ns && s->key_small_grid == grid2 &&
+                    s->key_small_threads == threads2 && s->key_small_smem == smem2;
   if (!same) {
     drop_graph(s);
     cudaGraph_t g = nullptr;
@@ -595,14 +642,33 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
     if (e == cudaSuccess) {
       cudaMemcpyAsync(s->d_descs, s->h_descs, nd * sizeof(Desc), cudaMemcpyHostToDevice, s->cap);
       cudaMemcpyAsync(s->d_units, s->h_units, nu * sizeof(int4), cudaMemcpyHostToDevice, s->cap);
-      cudaMemsetAsync(s->d_ctl, 0, 2 * sizeof(int), s->cap);
+      cudaMemsetAsync(s->d_ctl, 0, 4 * sizeof(int), s->cap);
       cudaMemsetAsync(s->d_done, 0, 5 * nd * sizeof(int), s->cap);
-      cudaError_t le = dtype == FS_F64
-                           ? Launch<double>::batch(s->d_descs, s->d_units, (int)nu, s->d_ctl, s->d_done,
-                                                   grid, threads, smem, wait_ns, s->cap)
-                           : Launch<float>::batch(s->d_descs, s->d_units, (int)nu, s->d_ctl, s->d_done,
-                                                  grid, threads, smem, wait_ns, s->cap);
-      cudaMemcpyAsync(s->h_status, s->d_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->cap);
+      cudaError_t le = cudaSuccess;
+      // the two launches are independent branches of the graph (no unit of
+      // one waits on the other's); the small CTAs take SMs as the
+      // persistent CTAs retire, or beside them where they fit
+      if (ns > 0) {
+        le = cudaEventRecord(s->ev_fork, s->cap);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(s->cap2, s->ev_fork, 0);
+      }
+      if (le == cudaSuccess)
+        le = dtype == FS_F64 ? Launch<double>::batch(s->d_descs, s->d_units, nm, s->d_ctl, s->d_done, grid,
+                                                     threads, smem, wait_ns, s->cap)
+                             : Launch<float>::batch(s->d_descs, s->d_units, nm, s->d_ctl, s->d_done, grid,
+                                                    threads, smem, wait_ns, s->cap);
+      if (ns > 0) {
+        if (le == cudaSuccess)
+          le = dtype == FS_F64 ? Launch<double>::batch(s->d_descs, s->d_units + nm, ns, s->d_ctl + 2, s->d_done,
+                                                       grid2, threads2, smem2, wait_ns, s->cap2)
+                               : Launch<float>::batch(s->d_descs, s->d_units + nm, ns, s->d_ctl + 2, s->d_done,
+                                                      grid2, threads2, smem2, wait_ns, s->cap2);
+        // join the branch whatever happened, so that the capture can end
+        const cudaError_t je = cudaEventRecord(s->ev_join, s->cap2);
+        const cudaError_t we = je == cudaSuccess ? cudaStreamWaitEvent(s->cap, s->ev_join, 0) : je;
+        if (le == cudaSuccess) le = we;
+      }
+      cudaMemcpyAsync(s->h_status, s->d_ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s->cap);
       e = cudaStreamEndCapture(s->cap, &g);
       if (e == cudaSuccess && le != cudaSuccess) e = le;
     }
@@ -619,8 +685,12 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
     s->key_smem = smem;
     s->key_wait = wait_ns;
     s->key_threads = threads;
+    s->key_small_units = ns;
+    s->key_small_grid = grid2;
+    s->key_small_threads = threads2;
+    s->key_small_smem = smem2;
   } else {
-    g_launches.fetch_add(1, std::memory_order_relaxed);  // the replayed k_batch
+    g_launches.fetch_add(ns > 0 ? 2 : 1, std::memory_order_relaxed);  // the replayed k_batch launches
   }
   {
     ProfScope ps(PC_BATCH, stream);
@@ -677,7 +747,7 @@ extern "C" fs_status fs_batch_wait(uint64_t ticket, int timeout_us) {
   int status = 0;
   if (s->pending && s->ticket == ticket) {
     s->pending = false;
-    status = s->h_status[1];
+    status = slot_status(s);
     remember(ticket, status);
   } else {
     for (auto &f : g_finished)

@@ -18,6 +18,12 @@ struct BatchPlan {
   size_t smem = 0;
   int dtype = -1;
   int threads = 512;             // batch CTA size: 256 when every unit fits (two CTAs per SM)
+  // single-CTA small problems of a batch that also has work units: their
+  // units are the last n_small_units of the table and run as a second,
+  // concurrent launch of small_threads-thread CTAs with small_smem bytes
+  int n_small_units = 0;
+  int small_threads = 512;
+  size_t small_smem = 0;
 };
 
 // Validate requests and build descriptors + work table (no device work).

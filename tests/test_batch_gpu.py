@@ -209,7 +209,9 @@ def test_outputs_in_pinned_host_memory(gpu_lib):
 
 
 def test_bounded_wait_expires_without_fault(gpu_lib, monkeypatch):
-    probs = wl.batch_mix(seed=5, count=6, sizes=(512, 1024))
+    # the 64^2 problems run as the small problems' second launch beside the
+    # persistent one; the stall is injected into the persistent launch
+    probs = wl.batch_mix(seed=5, count=8, sizes=(64, 512, 1024))
     P = Problems(probs)
     try:
         monkeypatch.setenv("FS_BATCH_INJECT_STALL", "1")
