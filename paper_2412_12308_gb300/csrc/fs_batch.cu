@@ -299,20 +299,26 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
       if (cc < 1) cc = 1;
       while (cc > 1 && (size_t)padded_len(cc * d.ny) * cs > 100 * 1024) cc >>= 1;
       d.cols_per_unit = cc;
-      // single-field FP32 power-of-two columns: each column group is staged
-      // into shared memory by one bulk copy while the previous one computes
-      if (bp->dtype == FS_F32 && !d.small && d.rp_col.e == 16 && p2_col_ok(d.ny) && !col_two_fields(d) &&
-          !(d.flags & F_SOURCE) && tma_enabled())
+      // single-field FP32 columns of compiled lengths (powers of two with
+      // tile 16, 3 x 2^k / 5 x 2^k with their family's tile): each column
+      // group is staged into shared memory by one bulk copy while the
+      // previous one computes
+      const bool col_ct = (d.rp_col.e == 16 && p2_col_ok(d.ny)) || (mx_col_ok(d.ny) && d.rp_col.e == mx_e(d.ny));
+      if (bp->dtype == FS_F32 && !d.small && col_ct && !col_two_fields(d) && !(d.flags & F_SOURCE) &&
+          tma_enabled())
         d.flags |= F_COL_TMA;
       int rr = d.rows_per_unit;  // the plan's row tile
       if (rr * tr > bp->threads) rr = std::max(1, bp->threads / tr);
       d.rows_per_unit = rr;
       d.n_row_units = (d.ny + rr - 1) / rr;
-      // C2R tiles of an even number of FP32 power-of-two rows: each tile is
-      // staged into shared memory by asynchronous copies while the previous
-      // one computes
-      if (bp->dtype == FS_F32 && !d.small && d.rp_row.e == 16 && p2_row_ok(d.M) && rr % 2 == 0 &&
-          (rr == p2_row_cnt(d.M) || rr == p2_row_cnt_256(d.M) || rr == p2_row_cnt_128(d.M)) && tma_enabled())
+      // C2R tiles of an even number of FP32 rows of compiled lengths and
+      // tile heights: each tile is staged into shared memory by asynchronous
+      // copies while the previous one computes
+      const bool row_p2 = d.rp_row.e == 16 && p2_row_ok(d.M) &&
+                          (rr == p2_row_cnt(d.M) || rr == p2_row_cnt_256(d.M) || rr == p2_row_cnt_128(d.M));
+      const bool row_mx = mx_row_ok(d.M) && d.rp_row.e == mx_e(d.M) &&
+                          (rr == mx_row_cnt(d.M) || rr == mx_row_cnt_256(d.M));
+      if (bp->dtype == FS_F32 && !d.small && (row_p2 || row_mx) && rr % 2 == 0 && tma_enabled())
         d.flags |= F_ROW_STAGED;
       d.n_col_units = (d.M + 1 + cc - 1) / cc;
       if (d.small) {

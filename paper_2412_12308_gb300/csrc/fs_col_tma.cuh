@@ -1,6 +1,8 @@
 // fs_col_tma.cuh -- column groups staged into shared memory by bulk copies
-// (FP32, power-of-two column lengths, register tile 16).  Used by the
-// standalone persistent column kernel and inlined into the batch kernel.
+// (FP32; power-of-two column lengths with register tile 16, 3 x 2^k / 5 x 2^k
+// lengths with their family's tile, 24 / 20).  Used by the standalone
+// persistent column kernel, inlined into the batch kernel (powers of two) and
+// called from it (the other two families, fs_mixed_f32.cu).
 #pragma once
 #include "fs_tma.cuh"
 #include "fs_units.cuh"
@@ -26,7 +28,7 @@ template <int L, int CC>
 __device__ __forceinline__ bool col_tma_groups(const Desc &d, int g_first, int g_step, int g_end, int cc_rt,
                                                cx<float> *buf0, cx<float> *buf1, uint64_t *bars, uint32_t &ph,
                                                int *s_abort) {
-  constexpr int E = 16, Tseg = L / E;
+  constexpr int E = mx_e(L) ? mx_e(L) : 16, Tseg = L / E;
   const int cc = CC ? CC : cc_rt;
   const int tid = threadIdx.x;
   const int rho = tid / Tseg, t = tid - rho * Tseg;

@@ -103,7 +103,7 @@ __device__ __forceinline__ int col_tma_unit(const Desc &d, int c0, int c1, int c
     case 2048: return col_tma_unit_l<2048>(d, c0, c1, cnt, sm, bars, ph, s_abort);
     case 4096: return col_tma_unit_l<4096>(d, c0, c1, cnt, sm, bars, ph, s_abort);
     case 8192: return col_tma_unit_l<8192>(d, c0, c1, cnt, sm, bars, ph, s_abort);
-    default: return 0;
+    default: return mx_col_tma_unit(d, c0, c1, cnt, sm, bars, &ph, s_abort);  // 3 x 2^k, 5 x 2^k
   }
 }
 
@@ -245,9 +245,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : (THREADS == 256 
         if constexpr (sizeof(T) == 4) {
           if (d.flags & F_ROW_STAGED) {
             const int t0 = u.z * d.row_g, t1 = min(tiles, t0 + d.row_g);
-            if (c2r_staged_unit(d, t0, t1, d.rows_per_unit, sm,
-                                reinterpret_cast<const cx<float> *>(u.w ? d.work_v : d.work_u),
-                                reinterpret_cast<float *>(u.w ? d.out_v : d.out_u)))
+            const cx<float> *spec = reinterpret_cast<const cx<float> *>(u.w ? d.work_v : d.work_u);
+            float *out = reinterpret_cast<float *>(u.w ? d.out_v : d.out_u);
+            if (c2r_staged_unit(d, t0, t1, d.rows_per_unit, sm, spec, out) ||
+                mx_c2r_staged_unit(d, t0, t1, d.rows_per_unit, sm, spec, out))
               break;
           }
         }

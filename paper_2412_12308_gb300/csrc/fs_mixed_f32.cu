@@ -1,7 +1,9 @@
 // FP32 pass kernels and batch units for the lengths 3 x 2^k and 5 x 2^k with
 // compile-time transform lengths (see fs_mixed.h).  FS_MX_ODD selects the
 // family compiled into this object (3 or 5), so the two compile in parallel.
+#include "fs_col_tma.cuh"
 #include "fs_mixed.h"
+#include "fs_row_async.cuh"
 #include "fs_units.cuh"
 
 #ifndef FS_MX_ODD
@@ -91,6 +93,62 @@ __device__ bool FS_CAT(mx_unit_col1_, FS_MX_SUFFIX)(const Desc &d, int unit, int
     mx_col1_unit<l>(d, unit, cnt, sm, wu, wv, sh); \
     return true;
     FS_MX_COLS(C)
+#undef C
+    default:
+      return false;
+  }
+}
+
+// Staged batch units: column groups by bulk copies, C2R tiles by
+// asynchronous copies, the next group / tile copied in while the current one
+// computes (same arithmetic as the unstaged units above).  Called, not
+// inlined, from the batch kernel so that its own code stays small.
+template <int L>
+__device__ __noinline__ int mx_col_tma_l(const Desc &d, int c0, int c1, int cnt, cx<float> *sm, uint64_t *bars,
+                                         uint32_t *ph, int *s_abort) {
+  const int plen = (padded_len(cnt * L) + 1) & ~1;  // even: the second buffer stays 16-byte aligned
+  uint32_t p = *ph;
+  const bool ok = col_tma_groups<L, 0>(d, c0, cnt, c1, cnt, sm, sm + plen, bars, p, s_abort);
+  *ph = p;
+  return ok ? 1 : -1;
+}
+template <int M, int CC>
+__device__ __noinline__ void mx_c2r_staged_l(const Desc &d, int tile0, int tile1, cx<float> *sm,
+                                             const cx<float> *spec, float *out) {
+  c2r_staged_tiles<M, CC>(d, tile0, tile1, sm, spec, out);
+}
+
+__device__ int FS_CAT(mx_col_tma_unit_, FS_MX_SUFFIX)(const Desc &d, int c0, int c1, int cnt, cx<float> *sm,
+                                                       uint64_t *bars, uint32_t *ph, int *s_abort) {
+  switch (d.ny) {
+#define C(l)                                                  \
+  case l:                                                     \
+    if (d.rp_col.e != mx_e(l)) return 0;                      \
+    return mx_col_tma_l<l>(d, c0, c1, cnt, sm, bars, ph, s_abort);
+    FS_MX_COLS(C)
+#undef C
+    default:
+      return 0;
+  }
+}
+__device__ bool FS_CAT(mx_c2r_staged_unit_, FS_MX_SUFFIX)(const Desc &d, int tile0, int tile1, int cnt,
+                                                           cx<float> *sm, const cx<float> *spec, float *out) {
+  switch (d.M) {
+#define C(m)                                                                                          \
+  case m:                                                                                             \
+    if (d.rp_row.e != mx_e(m)) return false;                                                          \
+    if constexpr (mx_row_cnt(m) % 2 == 0)                                                             \
+      if (cnt == mx_row_cnt(m)) {                                                                     \
+        mx_c2r_staged_l<m, mx_row_cnt(m)>(d, tile0, tile1, sm, spec, out);                            \
+        return true;                                                                                  \
+      }                                                                                               \
+    if constexpr (mx_row_cnt_256(m) != mx_row_cnt(m) && mx_row_cnt_256(m) % 2 == 0)                   \
+      if (cnt == mx_row_cnt_256(m)) {                                                                 \
+        mx_c2r_staged_l<m, mx_row_cnt_256(m)>(d, tile0, tile1, sm, spec, out);                        \
+        return true;                                                                                  \
+      }                                                                                               \
+    return false;
+    FS_MX_ROWS(C)
 #undef C
     default:
       return false;

@@ -1,6 +1,7 @@
 // fs_row_async.cuh -- C2R row tiles of the batch kernel staged into shared
-// memory by asynchronous copies (FP32, power-of-two row lengths, register
-// tile 16, an even number of rows per tile).
+// memory by asynchronous copies (FP32, an even number of rows per tile;
+// power-of-two row lengths with register tile 16, 3 x 2^k / 5 x 2^k lengths
+// with their family's tile, 24 / 20, instantiated in fs_mixed_f32.cu).
 #pragma once
 #include "fs_tma.cuh"
 #include "fs_units.cuh"
@@ -36,7 +37,7 @@ template <int M, int CC>
 __device__ __forceinline__ void c2r_staged_tiles(const Desc &d, int tile0, int tile1, cx<float> *sm,
                                                  const cx<float> *spec, float *out) {
   static_assert(CC % 2 == 0, "a 16-byte copy moves two rows of one frequency");
-  constexpr int E = 16, Tseg = M / E, LEN = c2r_stage_len(M, CC), HALF = CC / 2;
+  constexpr int E = mx_e(M) ? mx_e(M) : 16, Tseg = M / E, LEN = c2r_stage_len(M, CC), HALF = CC / 2;
   const int ny = d.ny, tid = threadIdx.x, nthr = blockDim.x;
   const int t = tid / CC, rho = tid - t * CC;
   auto issue = [&](cx<float> *b, int tile) {

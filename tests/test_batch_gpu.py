@@ -235,8 +235,11 @@ def test_bounded_wait_expires_without_fault(gpu_lib, monkeypatch):
 
 # (nx, ny): power-of-two rows and columns (staged), a ragged last C2R tile
 # (ny = 40 with 16-row tiles), rows of 8192 (one-row tiles: unstaged),
-# non-power-of-two columns (unstaged columns, staged rows)
-STAGED_SHAPES = [(256, 40), (1024, 96), (2048, 256), (512, 512), (1024, 1024), (8192, 128)]
+# columns of 96 (no compiled length: unstaged columns, staged rows);
+# 3 x 2^k and 5 x 2^k rows and columns (staged with tiles 24 / 20), one
+# with a ragged last C2R tile (rows of 640 points, 16-row tiles, ny = 40)
+STAGED_SHAPES = [(256, 40), (1024, 96), (2048, 256), (512, 512), (1024, 1024), (8192, 128),
+                 (1536, 768), (1280, 1536), (768, 160), (640, 40)]
 
 
 def staged_case():
@@ -245,12 +248,14 @@ def staged_case():
     in request order."""
     rng = np.random.default_rng(321)
     plans, states, outs, reqs = [], [], [], []
+    inputs = []  # the requests hold raw addresses: keep every input alive until the batch ends
     try:
         for nx, ny in STAGED_SHAPES:
             plan = fsolve.fs_plan_create(nx, ny, 1.0, 1.3, F32)
             plans.append(plan)
             f = torch.tensor(rng.standard_normal((ny, nx)), dtype=torch.float32, device="cuda")
             g = torch.tensor(rng.standard_normal((ny, nx)), dtype=torch.float32, device="cuda")
+            inputs += [f, g]
             s1, s2 = fsolve.fs_state_create(plan, f), fsolve.fs_state_create(plan, f, g)
             states += [s1, s2]
 
