@@ -223,17 +223,19 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 # for the CUDA sources they were taken on: any change to the sources makes the
 # reported traffic null until a new capture.
 # (workload, kernel class) -> {"bytes": DRAM bytes per launch, "sources_sha256": digest of csrc/}
-_SRC = "0a7ebacb8d90f93cf4ac3f209582f80951020093e3db62b2f90ea7fa0a6df763"
+_SRC = "96141551c7800c0b1637d5cf49f865045fb7054eb8c069d4d17a42d5621106f8"
 TRAFFIC_CAPTURES = {
     # profiles/k_batch_diffusion_1024.md
-    ("diffusion_1024", "batch"): {"bytes": 169_899_264 + 785_318_144, "sources_sha256": _SRC},
+    ("diffusion_1024", "batch"): {"bytes": 163_118_080 + 784_983_296, "sources_sha256": _SRC},
     # profiles/poisson_4096_pass_kernels.md
-    ("poisson_4096", "row_r2c"): {"bytes": 67_157_760 + 21_002_752, "sources_sha256": _SRC},
-    ("poisson_4096", "column"): {"bytes": 67_234_816 + 7_008_768, "sources_sha256": _SRC},
-    ("poisson_4096", "row_c2r"): {"bytes": 67_192_832 + 17_466_880, "sources_sha256": _SRC},
+    ("poisson_4096", "row_r2c"): {"bytes": 67_154_944 + 20_582_400, "sources_sha256": _SRC},
+    ("poisson_4096", "column"): {"bytes": 67_248_384 + 4_105_472, "sources_sha256": _SRC},
+    ("poisson_4096", "row_c2r"): {"bytes": 67_191_296 + 13_615_872, "sources_sha256": _SRC},
     # profiles/wave_4096_snapshots_and_batch_mix_traffic.md
-    ("wave_4096_snapshots", "column"): {"bytes": 67_221_248 + 7_789_568, "sources_sha256": _SRC},
-    ("batch_mix_512", "batch"): {"bytes": 3_932_552_704 + 4_320_621_568, "sources_sha256": _SRC},
+    ("wave_4096_snapshots", "column"): {"bytes": 67_243_264 + 8_174_080, "sources_sha256": _SRC},
+    # both launches of the batch: the persistent one and the small problems' one
+    ("batch_mix_512", "batch"): {"bytes": 4_052_630_784 + 4_825_443_840 + 13_404_672 + 1_236_992,
+                                 "sources_sha256": _SRC},
 }
 
 
