@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
@@ -320,6 +321,13 @@ fs_status plan_requests(const fs_request *reqs, int n, BatchPlan *bp, void *cons
                           (rr == mx_row_cnt(d.M) || rr == mx_row_cnt_256(d.M));
       if (bp->dtype == FS_F32 && !d.small && (row_p2 || row_mx) && rr % 2 == 0 && tma_enabled())
         d.flags |= F_ROW_STAGED;
+      // R2C tiles of the same lengths and heights: a tile (whole rows, one
+      // contiguous run of the real field) is staged by 16-byte asynchronous
+      // copies while the previous one computes; the field must be 16-byte aligned
+      const bool in_aligned = reinterpret_cast<uintptr_t>(d.in_u) % 16 == 0 &&
+                              reinterpret_cast<uintptr_t>(d.in_v) % 16 == 0;
+      if (bp->dtype == FS_F32 && !d.small && (row_p2 || row_mx) && in_aligned && tma_enabled())
+        d.flags |= F_R2C_STAGED;
       d.n_col_units = (d.M + 1 + cc - 1) / cc;
       if (d.small) {
         const int st = split_small ? bp->small_threads : bp->threads;
@@ -425,8 +433,10 @@ template <typename T>
 static size_t unit_smem(const Desc &d) {
   if (d.small) return Launch<T>::small_smem(d);
   const size_t col = (d.flags & F_COL_TMA) ? p2_col1_tma_unit_smem(d.ny, d.cols_per_unit) : Launch<T>::col_smem(d);
-  const size_t row = (d.flags & F_ROW_STAGED) ? 2 * (size_t)c2r_stage_len(d.M, d.rows_per_unit) * sizeof(cx<T>)
-                                               : Launch<T>::row_smem(d);
+  size_t row = (d.flags & F_ROW_STAGED) ? 2 * (size_t)c2r_stage_len(d.M, d.rows_per_unit) * sizeof(cx<T>)
+                                         : Launch<T>::row_smem(d);
+  if (d.flags & F_R2C_STAGED)
+    row = std::max(row, 2 * (size_t)r2c_stage_len(d.M, d.rows_per_unit) * sizeof(cx<T>));
   return std::max(row, col);
 }
 

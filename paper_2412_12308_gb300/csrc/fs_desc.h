@@ -26,7 +26,8 @@ enum Flags : int {
   F_WANT_V = 2,   // wave advance: also produce v = u_t
   F_SOURCE = 4,   // advance: a kept constant-source spectrum st_s is added
   F_COL_TMA = 8,     // batch: column units stage each column group by a bulk copy
-  F_ROW_STAGED = 16  // batch: C2R row units stage each tile by asynchronous copies
+  F_ROW_STAGED = 16,  // batch: C2R row units stage each tile by asynchronous copies
+  F_R2C_STAGED = 32   // batch: R2C row units stage each tile by asynchronous copies
 };
 
 // Unit kinds of the persistent batch kernel, in dependency order.

@@ -206,6 +206,16 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : (THREADS == 256 
         break;
       case K_ROW: {
         const int tiles = (d.ny + d.rows_per_unit - 1) / d.rows_per_unit;
+        if constexpr (sizeof(T) == 4) {
+          if (d.flags & F_R2C_STAGED) {
+            const int t0 = u.z * d.row_g, t1 = min(tiles, t0 + d.row_g);
+            const float *in = reinterpret_cast<const float *>(u.w ? d.in_v : d.in_u);
+            cx<float> *spec = reinterpret_cast<cx<float> *>(u.w ? d.work_v : d.work_u);
+            if (p2_r2c_staged_unit(d, t0, t1, d.rows_per_unit, sm, in, spec) ||
+                mx_r2c_staged_unit(d, t0, t1, d.rows_per_unit, sm, in, spec))
+              break;
+          }
+        }
         for (int g = 0; g < d.row_g; ++g) {
           const int tile = u.z * d.row_g + g;
           if (tile >= tiles) break;

@@ -45,6 +45,8 @@ constexpr int mx_row_cnt_256(int M) {
                                    cx<float> *wv, bool sh);                                                   \
   __device__ int mx_col_tma_unit_##F(const Desc &d, int c0, int c1, int cnt, cx<float> *sm, uint64_t *bars,    \
                                      uint32_t *ph, int *s_abort);                                            \
+  __device__ bool mx_r2c_staged_unit_##F(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,         \
+                                         const float *in, cx<float> *spec);                                   \
   __device__ bool mx_c2r_staged_unit_##F(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,         \
                                          const cx<float> *spec, float *out);                                  \
   PassKernel mx_r2c_f32_##F(int M);                                                                          \
@@ -72,14 +74,20 @@ __device__ __forceinline__ bool mx_unit_col1(const Desc &d, int unit, int cnt, c
                 : (o == 5 && mx_unit_col1_5(d, unit, cnt, sm, wu, wv, sh));
 }
 
-// Staged batch units (column groups by bulk copies, C2R tiles by asynchronous
-// copies): 0 / false when the length, tile or tile height is not compiled;
+// Staged batch units (column groups by bulk copies, R2C and C2R tiles by
+// asynchronous copies): 0 / false when the length, tile or tile height is not compiled;
 // the column unit returns -1 when a copy timed out (as col_tma_groups).
 __device__ __forceinline__ int mx_col_tma_unit(const Desc &d, int c0, int c1, int cnt, cx<float> *sm,
                                                uint64_t *bars, uint32_t *ph, int *s_abort) {
   const int o = mx_odd(d.ny);
   return o == 3 ? mx_col_tma_unit_3(d, c0, c1, cnt, sm, bars, ph, s_abort)
                 : (o == 5 ? mx_col_tma_unit_5(d, c0, c1, cnt, sm, bars, ph, s_abort) : 0);
+}
+__device__ __forceinline__ bool mx_r2c_staged_unit(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,
+                                                   const float *in, cx<float> *spec) {
+  const int o = mx_odd(d.M);
+  return o == 3 ? mx_r2c_staged_unit_3(d, tile0, tile1, cnt, sm, in, spec)
+                : (o == 5 && mx_r2c_staged_unit_5(d, tile0, tile1, cnt, sm, in, spec));
 }
 __device__ __forceinline__ bool mx_c2r_staged_unit(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,
                                                    const cx<float> *spec, float *out) {

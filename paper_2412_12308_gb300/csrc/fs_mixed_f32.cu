@@ -113,6 +113,11 @@ __device__ __noinline__ int mx_col_tma_l(const Desc &d, int c0, int c1, int cnt,
   return ok ? 1 : -1;
 }
 template <int M, int CC>
+__device__ __noinline__ void mx_r2c_staged_l(const Desc &d, int tile0, int tile1, cx<float> *sm, const float *in,
+                                             cx<float> *spec) {
+  r2c_staged_tiles<M, CC>(d, tile0, tile1, sm, in, spec);
+}
+template <int M, int CC>
 __device__ __noinline__ void mx_c2r_staged_l(const Desc &d, int tile0, int tile1, cx<float> *sm,
                                              const cx<float> *spec, float *out) {
   c2r_staged_tiles<M, CC>(d, tile0, tile1, sm, spec, out);
@@ -129,6 +134,28 @@ __device__ int FS_CAT(mx_col_tma_unit_, FS_MX_SUFFIX)(const Desc &d, int c0, int
 #undef C
     default:
       return 0;
+  }
+}
+__device__ bool FS_CAT(mx_r2c_staged_unit_, FS_MX_SUFFIX)(const Desc &d, int tile0, int tile1, int cnt,
+                                                           cx<float> *sm, const float *in, cx<float> *spec) {
+  switch (d.M) {
+#define C(m)                                                                 \
+  case m:                                                                    \
+    if (d.rp_row.e != mx_e(m)) return false;                                 \
+    if (cnt == mx_row_cnt(m)) {                                              \
+      mx_r2c_staged_l<m, mx_row_cnt(m)>(d, tile0, tile1, sm, in, spec);      \
+      return true;                                                           \
+    }                                                                        \
+    if constexpr (mx_row_cnt_256(m) != mx_row_cnt(m))                        \
+      if (cnt == mx_row_cnt_256(m)) {                                        \
+        mx_r2c_staged_l<m, mx_row_cnt_256(m)>(d, tile0, tile1, sm, in, spec); \
+        return true;                                                         \
+      }                                                                      \
+    return false;
+    FS_MX_ROWS(C)
+#undef C
+    default:
+      return false;
   }
 }
 __device__ bool FS_CAT(mx_c2r_staged_unit_, FS_MX_SUFFIX)(const Desc &d, int tile0, int tile1, int cnt,

@@ -37,6 +37,10 @@ __device__ bool p2_unit_c2r(const Desc &d, int unit, int cnt, cx<float> *sm, con
                             bool sh);
 __device__ bool p2_unit_col1(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu, cx<float> *wv,
                              bool sh);
+// Staged R2C row tiles tile0 .. tile1-1 of a batch unit (FP32, rows of a
+// compiled length and tile height; false otherwise): fs_row_async.cuh.
+__device__ bool p2_r2c_staged_unit(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm, const float *in,
+                                   cx<float> *spec);
 // columns of an advance with a constant source, one or two fields
 __device__ bool p2_unit_cols(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu, cx<float> *wv,
                              bool sh);

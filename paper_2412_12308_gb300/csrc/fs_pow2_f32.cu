@@ -1,6 +1,7 @@
 // FP32 pass kernels specialised for power-of-two lengths (see fs_pow2.h).
 #include "fs_col_tma.cuh"
 #include "fs_pow2.h"
+#include "fs_row_async.cuh"
 #include "fs_tma.cuh"
 #include "fs_units.cuh"
 
@@ -159,6 +160,42 @@ __device__ __forceinline__ bool p2_c2r_try(const Desc &d, int unit, int cnt, cx<
     }
   }
   return false;
+}
+
+// Staged R2C row tiles of a batch unit (F_R2C_STAGED): called, not inlined,
+// so that the batch kernel's own code stays small.
+template <int M, int CC>
+__device__ __noinline__ void p2_r2c_staged_l(const Desc &d, int tile0, int tile1, cx<float> *sm, const float *in,
+                                             cx<float> *spec) {
+  r2c_staged_tiles<M, CC>(d, tile0, tile1, sm, in, spec);
+}
+template <int M, int CC>
+__device__ __forceinline__ bool p2_r2c_staged_try(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,
+                                                  const float *in, cx<float> *spec) {
+  if constexpr (CC > 0) {
+    if (cnt == CC) {
+      p2_r2c_staged_l<M, CC>(d, tile0, tile1, sm, in, spec);
+      return true;
+    }
+  }
+  return false;
+}
+__device__ bool p2_r2c_staged_unit(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm, const float *in,
+                                   cx<float> *spec) {
+  if (d.rp_row.e != 16) return false;
+  switch (d.M) {
+#define C(m)                                                                                                   \
+  case m:                                                                                                      \
+    return p2_r2c_staged_try<m, p2_row_cnt(m)>(d, tile0, tile1, cnt, sm, in, spec) ||                         \
+           p2_r2c_staged_try<m, (p2_row_cnt_256(m) != p2_row_cnt(m) ? p2_row_cnt_256(m) : 0)>(d, tile0, tile1, \
+                                                                                              cnt, sm, in, spec) || \
+           p2_r2c_staged_try<m, (p2_row_cnt_128(m) != p2_row_cnt_256(m) ? p2_row_cnt_128(m) : 0)>(            \
+               d, tile0, tile1, cnt, sm, in, spec);
+    FS_P2_ROWS(C)
+#undef C
+    default:
+      return false;
+  }
 }
 
 // tile heights: standalone kernels, 256-thread and 128-thread batch CTAs

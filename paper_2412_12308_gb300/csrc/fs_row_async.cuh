@@ -76,6 +76,75 @@ __device__ __forceinline__ void c2r_staged_tiles(const Desc &d, int tile0, int t
   }
 }
 
+// Elements of one R2C staging buffer: the tile's real rows as pairs, row r
+// at r * r2c_row_stride (a pad after each row keeps the threads' reads of
+// their row's slots on distinct banks), or the padded FFT exchange of the
+// same rows, whichever is larger; even (16-byte aligned second buffer).
+__host__ __device__ constexpr int r2c_row_stride(int M, int cnt) { return M + (cnt <= 8 ? 16 / cnt : 2); }
+__host__ __device__ constexpr int r2c_stage_len(int M, int cnt) {
+  return ((padded_len(M * cnt) > cnt * r2c_row_stride(M, cnt) ? padded_len(M * cnt) : cnt * r2c_row_stride(M, cnt)) +
+          1) & ~1;
+}
+
+// One staged R2C tile: rows tile*CC .. of the tile copied into `cur` (row r
+// at r * r2c_row_stride), which then doubles as the FFT exchange area.  Kept
+// out of line so that the copy loop around it holds few registers.
+template <int M, int CC>
+__device__ __noinline__ void r2c_staged_tile(const Desc &d, int tile, cx<float> *cur, cx<float> *spec) {
+  constexpr int E = mx_e(M) ? mx_e(M) : 16, Tseg = M / E, RS = r2c_row_stride(M, CC);
+  const int tid = threadIdx.x;
+  const int t = tid / CC, rho = tid - t * CC;
+  const int y = tile * CC + rho;
+  const bool active = (t < Tseg) && (y < d.ny);
+  cx<float> v[E];
+  if (active) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = cur[rho * RS + t + Tseg * s];
+  } else {
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = zero_cx<float>();
+  }
+  // no barrier here: the transform's first exchange store into `cur` comes
+  // after its own barrier, which every read above precedes
+  r2c_tile_finish<float, E, M, CC>(d, CC, t, rho, y, active, v, cur, spec);
+}
+
+// Row R2C tiles tile0 .. tile1-1 (CC rows each) of one real field.  A
+// tile's rows are one contiguous run of the field; it is copied into shared
+// memory by 16-byte asynchronous copies (two pairs of one row each) while the
+// previous tile is transformed (two buffers).  Needs `in` 16-byte aligned
+// (the host checks); rows past ny (a ragged last tile) are neither copied
+// nor stored.
+template <int M, int CC>
+__device__ __forceinline__ void r2c_staged_tiles(const Desc &d, int tile0, int tile1, cx<float> *sm,
+                                                 const float *in, cx<float> *spec) {
+  constexpr int LEN = r2c_stage_len(M, CC), RS = r2c_row_stride(M, CC), Q = M / 2;  // 16-byte chunks per row
+  const int ny = d.ny, tid = threadIdx.x, nthr = blockDim.x;
+  auto issue = [&](cx<float> *b, int tile) {
+    const int y0 = tile * CC, rows = min(CC, ny - y0);
+    const float *src = in + (size_t)y0 * (2 * M);
+#pragma unroll 1
+    for (int idx = tid; idx < rows * Q; idx += nthr) {
+      const int r = idx / Q, q = idx - r * Q;
+      cp_async16(b + r * RS + 2 * q, src + (size_t)r * (2 * M) + 4 * q);
+    }
+    cp_async_commit();
+  };
+  issue(sm, tile0);
+#pragma unroll 1
+  for (int tile = tile0, i = 0; tile < tile1; ++tile, ++i) {
+    cx<float> *cur = (i & 1) ? sm + LEN : sm;
+    if (tile + 1 < tile1) {
+      issue((i & 1) ? sm : sm + LEN, tile + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    r2c_staged_tile<M, CC>(d, tile, cur, spec);
+  }
+}
+
 template <int M, int CC>
 __device__ __forceinline__ bool c2r_staged_try(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,
                                                const cx<float> *spec, float *out) {

@@ -52,6 +52,43 @@ __device__ __forceinline__ cx<T> zero_cx() {
 }
 
 // ------------------------------------------------------------ row R2C
+// The rest of a row R2C tile once thread (t, rho) holds its row's complex
+// pairs z_m, m = t + Tseg*s, in v (row y; `active` as in unit_row_r2c_t):
+// length-M FFT through the exchange buffer sm, then the R2C post-process into
+// spec[a][y].  Shared by the loading units below and the staged batch tiles.
+template <typename T, int E, int MC, int CC>
+__device__ __forceinline__ void r2c_tile_finish(const Desc &d, int cnt, int t, int rho, int y, bool active,
+                                                cx<T> (&v)[E], cx<T> *sm, cx<T> *spec) {
+  const int M = MC ? MC : d.M, ny = d.ny, Tseg = M / E;
+  const XLayout lay{rho, cnt};
+  const cx<T> *tw = reinterpret_cast<const cx<T> *>(d.tw_x);
+  fft_any<T, E, MC, CC, 2>(v, sm, lay, active, t, Tseg, M, d.rp_row, tw);
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) sm[padi(rho + (t + Tseg * s) * cnt)] = v[s];
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      const int k = t + Tseg * s;
+      const cx<T> zk = v[s];
+      if (k == 0) {
+        spec[y] = mk<T>(zk.x + zk.y, T(0));
+        spec[(size_t)M * ny + y] = mk<T>(zk.x - zk.y, T(0));
+      } else {
+        const cx<T> zm = conj(sm[padi(rho + (M - k) * cnt)]);
+        const cx<T> ev = T(0.5) * (zk + zm);
+        const cx<T> df_ = zk - zm;
+        const cx<T> od = mk<T>(T(0.5) * df_.y, T(-0.5) * df_.x);  // (zk - zm) / (2i)
+        spec[(size_t)k * ny + y] = ev + cmul(tw[k], od);
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // Rows y0..y0+cnt-1 of a real field -> spec[a][y] for a = 0..M.
 // Thread (t, rho) = (tid / cnt, tid % cnt) transforms row y0+rho; it holds
 // z_m = x_{2m} + i x_{2m+1} for m = t + Tseg*s.  After the length-M complex
@@ -70,8 +107,6 @@ __device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt_
   const int t = tid / cnt, rho = tid - t * cnt;
   const int y = unit * cnt + rho;
   const bool active = (t < Tseg) && (y < ny);
-  const XLayout lay{rho, cnt};
-  const cx<T> *tw = reinterpret_cast<const cx<T> *>(d.tw_x);
   cx<T> v[E];
   if constexpr (std::is_void<GEN>::value) {
     // the tile's rows are contiguous runs of M pairs: load them with all the
@@ -101,31 +136,7 @@ __device__ __forceinline__ void unit_row_r2c_t(const Desc &d, int unit, int cnt_
       for (int s = 0; s < E; ++s) v[s] = zero_cx<T>();
     }
   }
-  fft_any<T, E, MC, CC, 2>(v, sm, lay, active, t, Tseg, M, d.rp_row, tw);
-  __syncthreads();
-  if (active) {
-#pragma unroll
-    for (int s = 0; s < E; ++s) sm[padi(rho + (t + Tseg * s) * cnt)] = v[s];
-  }
-  __syncthreads();
-  if (active) {
-#pragma unroll
-    for (int s = 0; s < E; ++s) {
-      const int k = t + Tseg * s;
-      const cx<T> zk = v[s];
-      if (k == 0) {
-        spec[y] = mk<T>(zk.x + zk.y, T(0));
-        spec[(size_t)M * ny + y] = mk<T>(zk.x - zk.y, T(0));
-      } else {
-        const cx<T> zm = conj(sm[padi(rho + (M - k) * cnt)]);
-        const cx<T> ev = T(0.5) * (zk + zm);
-        const cx<T> df_ = zk - zm;
-        const cx<T> od = mk<T>(T(0.5) * df_.y, T(-0.5) * df_.x);  // (zk - zm) / (2i)
-        spec[(size_t)k * ny + y] = ev + cmul(tw[k], od);
-      }
-    }
-  }
-  __syncthreads();
+  r2c_tile_finish<T, E, MC, CC>(d, cnt, t, rho, y, active, v, sm, spec);
 }
 
 // ------------------------------------------------------------ row C2C (complex fields)
