@@ -9,6 +9,51 @@
 
 namespace fs {
 
+// The work on one staged group: columns g .. g+cc-1 (below g_end) in `cur`
+// ([column][L], unpadded), which then doubles as the FFT exchange area.
+template <int L>
+__device__ __forceinline__ void col_tma_group(const Desc &d, int g, int g_end, int cc, cx<float> *cur) {
+  constexpr int E = mx_e(L) ? mx_e(L) : 16, Tseg = L / E;
+  const int tid = threadIdx.x;
+  const int rho = tid / Tseg, t = tid - rho * Tseg;
+  const bool adv = (d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV);
+  cx<float> *dst = reinterpret_cast<cx<float> *>(d.work_u);
+  const cx<float> *tw = reinterpret_cast<const cx<float> *>(d.tw_y);
+  const int a = g + rho;
+  const bool active = rho < cc && a < g_end;
+  cx<float> u[E];
+  if (active) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) u[s] = cur[rho * L + t + Tseg * s];
+  } else {
+#pragma unroll
+    for (int s = 0; s < E; ++s) u[s] = zero_cx<float>();
+  }
+  const XLayout lay{rho * L, 1};
+  if (!adv) fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
+  if (!adv && d.st_out_u && active) {  // keep the forward spectrum
+    cx<float> *ou = reinterpret_cast<cx<float> *>(d.st_out_u) + (size_t)a * L;
+#pragma unroll
+    for (int s = 0; s < E; ++s) ou[t + Tseg * s] = u[s];
+  }
+  if (d.op != OP_FORWARD) {
+    if (active) col_op_single<float, E>(d, op_ctx<float>(d, a), t, Tseg, u);
+    // no barrier here: the transform's first exchange store into `cur`
+    // comes after its own barrier, which every read of `cur` above precedes
+    fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
+    if (active) {
+      cx<float> *o = dst + (size_t)a * L;
+#pragma unroll
+      for (int s = 0; s < E; ++s) o[t + Tseg * s] = conj(u[s]);
+    }
+  }
+}
+// the same out of line (a caller that keeps the copy loop's state in few registers)
+template <int L>
+__device__ __noinline__ void col_tma_group_ool(const Desc &d, int g, int g_end, int cc, cx<float> *cur) {
+  col_tma_group<L>(d, g, g_end, cc, cur);
+}
+
 // A column group is cc consecutive columns a = g .. g+cc-1: one contiguous run
 // of the x-frequency-major spectrum, so a single bulk copy (cp.async.bulk,
 // completion on an mbarrier) stages a whole group into shared memory.  The
@@ -24,18 +69,14 @@ namespace fs {
 // buffer 0.  Returns false when a copy did not land within kTmaWaitNs (the
 // device error word is set, and the copy still in flight has been waited for,
 // again bounded).
-template <int L, int CC>
+template <int L, int CC, bool OOL = false>
 __device__ __forceinline__ bool col_tma_groups(const Desc &d, int g_first, int g_step, int g_end, int cc_rt,
                                                cx<float> *buf0, cx<float> *buf1, uint64_t *bars, uint32_t &ph,
                                                int *s_abort) {
-  constexpr int E = mx_e(L) ? mx_e(L) : 16, Tseg = L / E;
   const int cc = CC ? CC : cc_rt;
   const int tid = threadIdx.x;
-  const int rho = tid / Tseg, t = tid - rho * Tseg;
   const bool adv = (d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV);
   const cx<float> *src = reinterpret_cast<const cx<float> *>(adv ? d.st_u : d.work_u);
-  cx<float> *dst = reinterpret_cast<cx<float> *>(d.work_u);
-  const cx<float> *tw = reinterpret_cast<const cx<float> *>(d.tw_y);
   auto issue = [&](cx<float> *b, uint64_t *bar, int g) {
     const int nc = min(cc, g_end - g);
     const uint32_t bytes = (uint32_t)(nc * L * sizeof(cx<float>));
@@ -78,34 +119,10 @@ __device__ __forceinline__ bool col_tma_groups(const Desc &d, int g_first, int g
       }
       return false;
     }
-    const int a = g + rho;
-    const bool active = rho < cc && a < g_end;
-    cx<float> u[E];
-    if (active) {
-#pragma unroll
-      for (int s = 0; s < E; ++s) u[s] = cur[rho * L + t + Tseg * s];
-    } else {
-#pragma unroll
-      for (int s = 0; s < E; ++s) u[s] = zero_cx<float>();
-    }
-    const XLayout lay{rho * L, 1};
-    if (!adv) fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
-    if (!adv && d.st_out_u && active) {  // keep the forward spectrum
-      cx<float> *ou = reinterpret_cast<cx<float> *>(d.st_out_u) + (size_t)a * L;
-#pragma unroll
-      for (int s = 0; s < E; ++s) ou[t + Tseg * s] = u[s];
-    }
-    if (d.op != OP_FORWARD) {
-      if (active) col_op_single<float, E>(d, op_ctx<float>(d, a), t, Tseg, u);
-      // no barrier here: the transform's first exchange store into `cur`
-      // comes after its own barrier, which every read of `cur` above precedes
-      fft_ct_from<float, E, L, 1, 1, 0>(u, cur, lay.base, active, t, tw);
-      if (active) {
-        cx<float> *o = dst + (size_t)a * L;
-#pragma unroll
-        for (int s = 0; s < E; ++s) o[t + Tseg * s] = conj(u[s]);
-      }
-    }
+    if constexpr (OOL)
+      col_tma_group_ool<L>(d, g, g_end, cc, cur);
+    else
+      col_tma_group<L>(d, g, g_end, cc, cur);
     fence_proxy_async_smem();
     __syncthreads();
   }

@@ -108,7 +108,7 @@ __device__ __noinline__ int mx_col_tma_l(const Desc &d, int c0, int c1, int cnt,
                                          uint32_t *ph, int *s_abort) {
   const int plen = (padded_len(cnt * L) + 1) & ~1;  // even: the second buffer stays 16-byte aligned
   uint32_t p = *ph;
-  const bool ok = col_tma_groups<L, 0>(d, c0, cnt, c1, cnt, sm, sm + plen, bars, p, s_abort);
+  const bool ok = col_tma_groups<L, 0, true>(d, c0, cnt, c1, cnt, sm, sm + plen, bars, p, s_abort);
   *ph = p;
   return ok ? 1 : -1;
 }
@@ -120,7 +120,7 @@ __device__ __noinline__ void mx_r2c_staged_l(const Desc &d, int tile0, int tile1
 template <int M, int CC>
 __device__ __noinline__ void mx_c2r_staged_l(const Desc &d, int tile0, int tile1, cx<float> *sm,
                                              const cx<float> *spec, float *out) {
-  c2r_staged_tiles<M, CC>(d, tile0, tile1, sm, spec, out);
+  c2r_staged_tiles<M, CC, true>(d, tile0, tile1, sm, spec, out);
 }
 
 __device__ int FS_CAT(mx_col_tma_unit_, FS_MX_SUFFIX)(const Desc &d, int c0, int c1, int cnt, cx<float> *sm,

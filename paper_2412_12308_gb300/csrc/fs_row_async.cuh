@@ -27,19 +27,46 @@ __host__ __device__ constexpr int c2r_stage_len(int M, int cnt) {
   return ((padded_len(M * cnt) > (M + 1) * cnt ? padded_len(M * cnt) : (M + 1) * cnt) + 1) & ~1;
 }
 
+// One staged C2R tile in `cur` ([a][row], unpadded), which then doubles as
+// the FFT exchange area: rows tile*CC .. of the output.
+template <int M, int CC>
+__device__ __forceinline__ void c2r_staged_tile(const Desc &d, int tile, cx<float> *cur, float *out) {
+  constexpr int E = mx_e(M) ? mx_e(M) : 16, Tseg = M / E;
+  const int tid = threadIdx.x;
+  const int t = tid / CC, rho = tid - t * CC;
+  const int y = tile * CC + rho;
+  const bool active = (t < Tseg) && (y < d.ny);
+  cx<float> v[E];
+  cx<float> xM = zero_cx<float>();
+  if (active) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = cur[rho + (t + Tseg * s) * CC];
+    if (t == 0) xM = cur[rho + M * CC];
+  } else {
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = zero_cx<float>();
+  }
+  c2r_tile_finish<float, E, M, CC>(d, tile, CC, t, rho, active, v, xM,
+                                   [&](int j) { return cur[rho + j * CC]; }, cur, out);
+}
+// the same out of line (a caller that keeps the copy loop's state in few registers)
+template <int M, int CC>
+__device__ __noinline__ void c2r_staged_tile_ool(const Desc &d, int tile, cx<float> *cur, float *out) {
+  c2r_staged_tile<M, CC>(d, tile, cur, out);
+}
+
 // Row tiles tile0 .. tile1-1 (CC rows each) of one field.  The tile after the
 // current one is copied in while the current one is transformed (two
 // buffers); a thread's copies complete without polling (cp.async.wait_group),
 // and the barrier after the wait makes every thread's copies visible.  The
 // current buffer then doubles as the FFT exchange area.  Rows past ny (a
 // ragged last tile) are neither copied nor stored.
-template <int M, int CC>
+template <int M, int CC, bool OOL = false>
 __device__ __forceinline__ void c2r_staged_tiles(const Desc &d, int tile0, int tile1, cx<float> *sm,
                                                  const cx<float> *spec, float *out) {
   static_assert(CC % 2 == 0, "a 16-byte copy moves two rows of one frequency");
-  constexpr int E = mx_e(M) ? mx_e(M) : 16, Tseg = M / E, LEN = c2r_stage_len(M, CC), HALF = CC / 2;
+  constexpr int LEN = c2r_stage_len(M, CC), HALF = CC / 2;
   const int ny = d.ny, tid = threadIdx.x, nthr = blockDim.x;
-  const int t = tid / CC, rho = tid - t * CC;
   auto issue = [&](cx<float> *b, int tile) {
     const int y0 = tile * CC, rows = min(CC, ny - y0);  // even: ny and CC are even
 #pragma unroll 1
@@ -59,20 +86,10 @@ __device__ __forceinline__ void c2r_staged_tiles(const Desc &d, int tile0, int t
       cp_async_wait<0>();
     }
     __syncthreads();
-    const int y = tile * CC + rho;
-    const bool active = (t < Tseg) && (y < ny);
-    cx<float> v[E];
-    cx<float> xM = zero_cx<float>();
-    if (active) {
-#pragma unroll
-      for (int s = 0; s < E; ++s) v[s] = cur[rho + (t + Tseg * s) * CC];
-      if (t == 0) xM = cur[rho + M * CC];
-    } else {
-#pragma unroll
-      for (int s = 0; s < E; ++s) v[s] = zero_cx<float>();
-    }
-    c2r_tile_finish<float, E, M, CC>(d, tile, CC, t, rho, active, v, xM,
-                                     [&](int j) { return cur[rho + j * CC]; }, cur, out);
+    if constexpr (OOL)
+      c2r_staged_tile_ool<M, CC>(d, tile, cur, out);
+    else
+      c2r_staged_tile<M, CC>(d, tile, cur, out);
   }
 }
 
