@@ -644,8 +644,25 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
     return set_error(FS_ERR_SIZE, "fs_batch_submit: batch kernel does not fit on an SM");
   int grid = sms * per_sm;
   if (grid > nm) grid = nm;
-  int grid2 = ns > 0 ? sms * per_sm2 : 0;
-  if (grid2 > ns) grid2 = ns;
+  // The small problems' launch runs beside the persistent one from the start
+  // on part of the GPU: its CTAs are dispatched first (high priority) and
+  // loop over the small problems, the persistent CTAs fill the remaining room
+  // and take the SMs it frees.  Its CTA count: enough that it ends well
+  // within the persistent launch's time (estimated at 1.5 TB/s over the
+  // units' bytes, ~150 us per single-CTA problem), at least a quarter of the
+  // SMs, at most one per SM (measured on GB300, 512-problem mix: 4.39 ms
+  // with one CTA per SM launched beside the persistent one).
+  int grid2 = 0;
+  if (ns > 0) {
+    double unit_bytes = 0.0;
+    for (size_t k = 0; k < nd; ++k)
+      if (!bp.descs[k].small && !bp.direct[k]) unit_bytes += 24.0 * (double)bp.descs[k].nx * bp.descs[k].ny;
+    const double t_main_us = unit_bytes / 1.5e6, t_small_us = 150.0;
+    const int cap = std::min(ns, sms * per_sm2);
+    grid2 = (int)std::ceil(ns * t_small_us / std::max(t_main_us, 1.0));
+    grid2 = std::max(grid2, std::min(cap, std::max(1, sms / 4)));
+    grid2 = std::min(grid2, cap);
+  }
 
   const bool same = s->gexec && s->key_descs == (int)nd && s->key_units == (int)nu && s->key_grid == grid &&
                     s->key_dtype == dtype && s->key_smem == smem && s->key_wait == wait_ns &&
@@ -662,23 +679,22 @@ fs_status batch_submit_internal(const fs_request *reqs, int n, void *const *keep
       cudaMemsetAsync(s->d_done, 0, 5 * nd * sizeof(int), s->cap);
       cudaError_t le = cudaSuccess;
       // the two launches are independent branches of the graph (no unit of
-      // one waits on the other's); the small CTAs take SMs as the
-      // persistent CTAs retire, or beside them where they fit
+      // one waits on the other's)
       if (ns > 0) {
         le = cudaEventRecord(s->ev_fork, s->cap);
         if (le == cudaSuccess) le = cudaStreamWaitEvent(s->cap2, s->ev_fork, 0);
       }
+      if (ns > 0 && le == cudaSuccess)
+        le = dtype == FS_F64 ? Launch<double>::batch(s->d_descs, s->d_units + nm, ns, s->d_ctl + 2, s->d_done,
+                                                     grid2, threads2, smem2, wait_ns, s->cap2, true)
+                             : Launch<float>::batch(s->d_descs, s->d_units + nm, ns, s->d_ctl + 2, s->d_done,
+                                                    grid2, threads2, smem2, wait_ns, s->cap2, true);
       if (le == cudaSuccess)
         le = dtype == FS_F64 ? Launch<double>::batch(s->d_descs, s->d_units, nm, s->d_ctl, s->d_done, grid,
                                                      threads, smem, wait_ns, s->cap)
                              : Launch<float>::batch(s->d_descs, s->d_units, nm, s->d_ctl, s->d_done, grid,
                                                     threads, smem, wait_ns, s->cap);
       if (ns > 0) {
-        if (le == cudaSuccess)
-          le = dtype == FS_F64 ? Launch<double>::batch(s->d_descs, s->d_units + nm, ns, s->d_ctl + 2, s->d_done,
-                                                       grid2, threads2, smem2, wait_ns, s->cap2)
-                               : Launch<float>::batch(s->d_descs, s->d_units + nm, ns, s->d_ctl + 2, s->d_done,
-                                                      grid2, threads2, smem2, wait_ns, s->cap2);
         // join the branch whatever happened, so that the capture can end
         const cudaError_t je = cudaEventRecord(s->ev_join, s->cap2);
         const cudaError_t we = je == cudaSuccess ? cudaStreamWaitEvent(s->cap, s->ev_join, 0) : je;

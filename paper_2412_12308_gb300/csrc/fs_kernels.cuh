@@ -422,12 +422,34 @@ struct Launch {
   static BatchKernel batch_kernel(int threads) {
     return threads == 128 ? k_batch<T, 128> : (threads == 256 ? k_batch<T, 256> : k_batch<T, kMaxThreads>);
   }
+  // high_priority: the launch's CTAs are dispatched before those of
+  // concurrently pending default-priority work (a launch attribute, kept
+  // when the launch is captured into a graph)
   static cudaError_t batch(const Desc *descs, const int4 *units, int n_units, int *ctl, int *done,
-                           int grid, int threads, size_t smem, unsigned long long wait_ns, cudaStream_t s) {
+                           int grid, int threads, size_t smem, unsigned long long wait_ns, cudaStream_t s,
+                           bool high_priority = false) {
     BatchKernel k = batch_kernel(threads);
     cudaError_t e = set_smem((const void *)k, smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, threads, smem, s>>>(descs, units, n_units, ctl, done, wait_ns);
+    if (!high_priority) {
+      k<<<grid, threads, smem, s>>>(descs, units, n_units, ctl, done, wait_ns);
+    } else {
+      int least = 0, greatest = 0;
+      e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+      if (e != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(threads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributePriority;
+      attr[0].val.priority = greatest;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, k, descs, units, n_units, ctl, done, wait_ns);
+      if (e != cudaSuccess) return e;
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
   }
