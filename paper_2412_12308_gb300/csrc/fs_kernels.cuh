@@ -103,7 +103,7 @@ __device__ __forceinline__ int col_tma_unit(const Desc &d, int c0, int c1, int c
     case 2048: return col_tma_unit_l<2048>(d, c0, c1, cnt, sm, bars, ph, s_abort);
     case 4096: return col_tma_unit_l<4096>(d, c0, c1, cnt, sm, bars, ph, s_abort);
     case 8192: return col_tma_unit_l<8192>(d, c0, c1, cnt, sm, bars, ph, s_abort);
-    default: return mx_col_tma_unit(d, c0, c1, cnt, sm, bars, &ph, s_abort);  // 3 x 2^k, 5 x 2^k
+    default: return mx_col_tma_unit(d, c0, c1, cnt, sm, bars, ph, s_abort);  // 3 x 2^k, 5 x 2^k
   }
 }
 

@@ -36,6 +36,14 @@ constexpr int mx_row_cnt_256(int M) {
 // Device units for the batch and single-CTA paths; false when the length,
 // tile or tile height is not compiled (the caller uses the runtime engine).
 // One object per family (fs_mixed_f32.cu with FS_MX_ODD = 3 or 5).
+// Result of a staged mixed-radix column unit: r as col_tma_unit (1 done, 0
+// not compiled, -1 a copy timed out) and the CTA's barrier parities after it
+// (returned, so that the caller's parity word stays in a register).
+struct MxColRet {
+  int r;
+  uint32_t ph;
+};
+
 #define FS_MX_DECL(F)                                                                                         \
   __device__ bool mx_unit_r2c_##F(const Desc &d, int unit, int cnt, cx<float> *sm, const float *in,           \
                                   cx<float> *spec);                                                           \
@@ -43,8 +51,8 @@ constexpr int mx_row_cnt_256(int M) {
                                   float *out, bool sh);                                                       \
   __device__ bool mx_unit_col1_##F(const Desc &d, int unit, int cnt, cx<float> *sm, cx<float> *wu,            \
                                    cx<float> *wv, bool sh);                                                   \
-  __device__ int mx_col_tma_unit_##F(const Desc &d, int c0, int c1, int cnt, cx<float> *sm, uint64_t *bars,    \
-                                     uint32_t *ph, int *s_abort);                                            \
+  __device__ MxColRet mx_col_tma_unit_##F(const Desc &d, int c0, int c1, int cnt, cx<float> *sm,              \
+                                          uint64_t *bars, uint32_t ph, int *s_abort);                         \
   __device__ bool mx_r2c_staged_unit_##F(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,         \
                                          const float *in, cx<float> *spec);                                   \
   __device__ bool mx_c2r_staged_unit_##F(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,         \
@@ -78,10 +86,13 @@ __device__ __forceinline__ bool mx_unit_col1(const Desc &d, int unit, int cnt, c
 // asynchronous copies): 0 / false when the length, tile or tile height is not compiled;
 // the column unit returns -1 when a copy timed out (as col_tma_groups).
 __device__ __forceinline__ int mx_col_tma_unit(const Desc &d, int c0, int c1, int cnt, cx<float> *sm,
-                                               uint64_t *bars, uint32_t *ph, int *s_abort) {
+                                               uint64_t *bars, uint32_t &ph, int *s_abort) {
   const int o = mx_odd(d.ny);
-  return o == 3 ? mx_col_tma_unit_3(d, c0, c1, cnt, sm, bars, ph, s_abort)
-                : (o == 5 ? mx_col_tma_unit_5(d, c0, c1, cnt, sm, bars, ph, s_abort) : 0);
+  if (o != 3 && o != 5) return 0;
+  const MxColRet r = o == 3 ? mx_col_tma_unit_3(d, c0, c1, cnt, sm, bars, ph, s_abort)
+                            : mx_col_tma_unit_5(d, c0, c1, cnt, sm, bars, ph, s_abort);
+  ph = r.ph;
+  return r.r;
 }
 __device__ __forceinline__ bool mx_r2c_staged_unit(const Desc &d, int tile0, int tile1, int cnt, cx<float> *sm,
                                                    const float *in, cx<float> *spec) {

@@ -104,13 +104,11 @@ __device__ bool FS_CAT(mx_unit_col1_, FS_MX_SUFFIX)(const Desc &d, int unit, int
 // computes (same arithmetic as the unstaged units above).  Called, not
 // inlined, from the batch kernel so that its own code stays small.
 template <int L>
-__device__ __noinline__ int mx_col_tma_l(const Desc &d, int c0, int c1, int cnt, cx<float> *sm, uint64_t *bars,
-                                         uint32_t *ph, int *s_abort) {
+__device__ __noinline__ MxColRet mx_col_tma_l(const Desc &d, int c0, int c1, int cnt, cx<float> *sm,
+                                              uint64_t *bars, uint32_t ph, int *s_abort) {
   const int plen = (padded_len(cnt * L) + 1) & ~1;  // even: the second buffer stays 16-byte aligned
-  uint32_t p = *ph;
-  const bool ok = col_tma_groups<L, 0, true>(d, c0, cnt, c1, cnt, sm, sm + plen, bars, p, s_abort);
-  *ph = p;
-  return ok ? 1 : -1;
+  const bool ok = col_tma_groups<L, 0, true>(d, c0, cnt, c1, cnt, sm, sm + plen, bars, ph, s_abort);
+  return MxColRet{ok ? 1 : -1, ph};
 }
 template <int M, int CC>
 __device__ __noinline__ void mx_r2c_staged_l(const Desc &d, int tile0, int tile1, cx<float> *sm, const float *in,
@@ -123,17 +121,17 @@ __device__ __noinline__ void mx_c2r_staged_l(const Desc &d, int tile0, int tile1
   c2r_staged_tiles<M, CC, true>(d, tile0, tile1, sm, spec, out);
 }
 
-__device__ int FS_CAT(mx_col_tma_unit_, FS_MX_SUFFIX)(const Desc &d, int c0, int c1, int cnt, cx<float> *sm,
-                                                       uint64_t *bars, uint32_t *ph, int *s_abort) {
+__device__ MxColRet FS_CAT(mx_col_tma_unit_, FS_MX_SUFFIX)(const Desc &d, int c0, int c1, int cnt, cx<float> *sm,
+                                                            uint64_t *bars, uint32_t ph, int *s_abort) {
   switch (d.ny) {
 #define C(l)                                                  \
   case l:                                                     \
-    if (d.rp_col.e != mx_e(l)) return 0;                      \
+    if (d.rp_col.e != mx_e(l)) return MxColRet{0, ph};        \
     return mx_col_tma_l<l>(d, c0, c1, cnt, sm, bars, ph, s_abort);
     FS_MX_COLS(C)
 #undef C
     default:
-      return 0;
+      return MxColRet{0, ph};
   }
 }
 __device__ bool FS_CAT(mx_r2c_staged_unit_, FS_MX_SUFFIX)(const Desc &d, int tile0, int tile1, int cnt,
