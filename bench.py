@@ -223,18 +223,18 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 # for the CUDA sources they were taken on: any change to the sources makes the
 # reported traffic null until a new capture.
 # (workload, kernel class) -> {"bytes": DRAM bytes per launch, "sources_sha256": digest of csrc/}
-_SRC = "96141551c7800c0b1637d5cf49f865045fb7054eb8c069d4d17a42d5621106f8"
+_SRC = "55e513f8bf32a898b28a1d1dfd4a63323bed5366061d8afd258730c160f246bb"
 TRAFFIC_CAPTURES = {
     # profiles/k_batch_diffusion_1024.md
-    ("diffusion_1024", "batch"): {"bytes": 163_118_080 + 784_983_296, "sources_sha256": _SRC},
+    ("diffusion_1024", "batch"): {"bytes": 169_153_792 + 783_524_352, "sources_sha256": _SRC},
     # profiles/poisson_4096_pass_kernels.md
-    ("poisson_4096", "row_r2c"): {"bytes": 67_154_944 + 20_582_400, "sources_sha256": _SRC},
-    ("poisson_4096", "column"): {"bytes": 67_248_384 + 4_105_472, "sources_sha256": _SRC},
-    ("poisson_4096", "row_c2r"): {"bytes": 67_191_296 + 13_615_872, "sources_sha256": _SRC},
+    ("poisson_4096", "row_r2c"): {"bytes": 67_154_944 + 20_872_960, "sources_sha256": _SRC},
+    ("poisson_4096", "column"): {"bytes": 67_263_488 + 4_386_304, "sources_sha256": _SRC},
+    ("poisson_4096", "row_c2r"): {"bytes": 67_193_088 + 13_507_328, "sources_sha256": _SRC},
     # profiles/wave_4096_snapshots_and_batch_mix_traffic.md
-    ("wave_4096_snapshots", "column"): {"bytes": 67_243_264 + 8_174_080, "sources_sha256": _SRC},
+    ("wave_4096_snapshots", "column"): {"bytes": 67_277_568 + 8_474_112, "sources_sha256": _SRC},
     # both launches of the batch: the persistent one and the small problems' one
-    ("batch_mix_512", "batch"): {"bytes": 4_052_630_784 + 4_825_443_840 + 13_404_672 + 1_236_992,
+    ("batch_mix_512", "batch"): {"bytes": 4_147_081_216 + 4_491_426_304 + 13_424_384 + 48_640,
                                  "sources_sha256": _SRC},
 }
 

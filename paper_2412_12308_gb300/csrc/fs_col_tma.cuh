@@ -11,14 +11,12 @@ namespace fs {
 
 // The work on one staged group: columns g .. g+cc-1 (below g_end) in `cur`
 // ([column][L], unpadded), which then doubles as the FFT exchange area.
+// (rho, t): the thread's column in the group and its slot; adv: an advance
+// (no forward transform); dst: the work spectrum; tw: the length-L twiddles.
 template <int L>
-__device__ __forceinline__ void col_tma_group(const Desc &d, int g, int g_end, int cc, cx<float> *cur) {
+__device__ __forceinline__ void col_tma_group(const Desc &d, int g, int g_end, int cc, cx<float> *cur, int rho,
+                                              int t, bool adv, cx<float> *dst, const cx<float> *tw) {
   constexpr int E = mx_e(L) ? mx_e(L) : 16, Tseg = L / E;
-  const int tid = threadIdx.x;
-  const int rho = tid / Tseg, t = tid - rho * Tseg;
-  const bool adv = (d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV);
-  cx<float> *dst = reinterpret_cast<cx<float> *>(d.work_u);
-  const cx<float> *tw = reinterpret_cast<const cx<float> *>(d.tw_y);
   const int a = g + rho;
   const bool active = rho < cc && a < g_end;
   cx<float> u[E];
@@ -50,8 +48,9 @@ __device__ __forceinline__ void col_tma_group(const Desc &d, int g, int g_end, i
 }
 // the same out of line (a caller that keeps the copy loop's state in few registers)
 template <int L>
-__device__ __noinline__ void col_tma_group_ool(const Desc &d, int g, int g_end, int cc, cx<float> *cur) {
-  col_tma_group<L>(d, g, g_end, cc, cur);
+__device__ __noinline__ void col_tma_group_ool(const Desc &d, int g, int g_end, int cc, cx<float> *cur, int rho,
+                                               int t, bool adv, cx<float> *dst, const cx<float> *tw) {
+  col_tma_group<L>(d, g, g_end, cc, cur, rho, t, adv, dst, tw);
 }
 
 // A column group is cc consecutive columns a = g .. g+cc-1: one contiguous run
@@ -73,10 +72,14 @@ template <int L, int CC, bool OOL = false>
 __device__ __forceinline__ bool col_tma_groups(const Desc &d, int g_first, int g_step, int g_end, int cc_rt,
                                                cx<float> *buf0, cx<float> *buf1, uint64_t *bars, uint32_t &ph,
                                                int *s_abort) {
+  constexpr int E = mx_e(L) ? mx_e(L) : 16, Tseg = L / E;
   const int cc = CC ? CC : cc_rt;
   const int tid = threadIdx.x;
+  const int rho = tid / Tseg, t = tid - rho * Tseg;
   const bool adv = (d.op == OP_DIFF_ADV || d.op == OP_WAVE_ADV);
   const cx<float> *src = reinterpret_cast<const cx<float> *>(adv ? d.st_u : d.work_u);
+  cx<float> *dst = reinterpret_cast<cx<float> *>(d.work_u);
+  const cx<float> *tw = reinterpret_cast<const cx<float> *>(d.tw_y);
   auto issue = [&](cx<float> *b, uint64_t *bar, int g) {
     const int nc = min(cc, g_end - g);
     const uint32_t bytes = (uint32_t)(nc * L * sizeof(cx<float>));
@@ -120,9 +123,9 @@ __device__ __forceinline__ bool col_tma_groups(const Desc &d, int g_first, int g
       return false;
     }
     if constexpr (OOL)
-      col_tma_group_ool<L>(d, g, g_end, cc, cur);
+      col_tma_group_ool<L>(d, g, g_end, cc, cur, rho, t, adv, dst, tw);
     else
-      col_tma_group<L>(d, g, g_end, cc, cur);
+      col_tma_group<L>(d, g, g_end, cc, cur, rho, t, adv, dst, tw);
     fence_proxy_async_smem();
     __syncthreads();
   }

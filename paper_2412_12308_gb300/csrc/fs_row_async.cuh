@@ -29,11 +29,11 @@ __host__ __device__ constexpr int c2r_stage_len(int M, int cnt) {
 
 // One staged C2R tile in `cur` ([a][row], unpadded), which then doubles as
 // the FFT exchange area: rows tile*CC .. of the output.
+// (t, rho): the thread's slot and row in the tile.
 template <int M, int CC>
-__device__ __forceinline__ void c2r_staged_tile(const Desc &d, int tile, cx<float> *cur, float *out) {
+__device__ __forceinline__ void c2r_staged_tile(const Desc &d, int tile, cx<float> *cur, float *out, int t,
+                                                int rho) {
   constexpr int E = mx_e(M) ? mx_e(M) : 16, Tseg = M / E;
-  const int tid = threadIdx.x;
-  const int t = tid / CC, rho = tid - t * CC;
   const int y = tile * CC + rho;
   const bool active = (t < Tseg) && (y < d.ny);
   cx<float> v[E];
@@ -51,8 +51,9 @@ __device__ __forceinline__ void c2r_staged_tile(const Desc &d, int tile, cx<floa
 }
 // the same out of line (a caller that keeps the copy loop's state in few registers)
 template <int M, int CC>
-__device__ __noinline__ void c2r_staged_tile_ool(const Desc &d, int tile, cx<float> *cur, float *out) {
-  c2r_staged_tile<M, CC>(d, tile, cur, out);
+__device__ __noinline__ void c2r_staged_tile_ool(const Desc &d, int tile, cx<float> *cur, float *out, int t,
+                                                 int rho) {
+  c2r_staged_tile<M, CC>(d, tile, cur, out, t, rho);
 }
 
 // Row tiles tile0 .. tile1-1 (CC rows each) of one field.  The tile after the
@@ -67,6 +68,7 @@ __device__ __forceinline__ void c2r_staged_tiles(const Desc &d, int tile0, int t
   static_assert(CC % 2 == 0, "a 16-byte copy moves two rows of one frequency");
   constexpr int LEN = c2r_stage_len(M, CC), HALF = CC / 2;
   const int ny = d.ny, tid = threadIdx.x, nthr = blockDim.x;
+  const int t = tid / CC, rho = tid - t * CC;
   auto issue = [&](cx<float> *b, int tile) {
     const int y0 = tile * CC, rows = min(CC, ny - y0);  // even: ny and CC are even
 #pragma unroll 1
@@ -87,9 +89,9 @@ __device__ __forceinline__ void c2r_staged_tiles(const Desc &d, int tile0, int t
     }
     __syncthreads();
     if constexpr (OOL)
-      c2r_staged_tile_ool<M, CC>(d, tile, cur, out);
+      c2r_staged_tile_ool<M, CC>(d, tile, cur, out, t, rho);
     else
-      c2r_staged_tile<M, CC>(d, tile, cur, out);
+      c2r_staged_tile<M, CC>(d, tile, cur, out, t, rho);
   }
 }
 
