@@ -356,7 +356,11 @@ typedef struct fs_request {
  * from a device work table through an atomic counter; a unit waits (bounded:
  * 2 s per wait by default, env FS_BATCH_WAIT_NS; expiry sets FS_ERR_TIMEOUT in
  * the batch status and the kernel exits) only for units of its own problem
- * listed before it.  Problems of 4096^2 points or more (env FS_BATCH_DIRECT_MIN)
+ * listed before it.  When a batch has both problems small enough to be
+ * solved whole by one CTA and problems run as units, the small ones run as a
+ * second launch in the same graph, beside the first (its own counter and
+ * status; the batch status is the first error of the two).  Problems of
+ * 4096^2 points or more (env FS_BATCH_DIRECT_MIN)
  * fill the GPU on their own and run as the standalone pass kernels, in order,
  * before that launch.  Workspace comes from a library-owned arena per in-flight
  * batch.  Each problem's result depends only on its own request (same tile
