@@ -3,7 +3,8 @@
 //
 // The engine computes the length-L DFT of Sec. II.B (Eq. DFT) with the
 // even/odd splitting idea of Sec. II.C generalised to radix R in
-// {2, 3, 4, 5, 8, 16} (a Stockham auto-sort decimation-in-time ordering, so
+// {2, 3, 4, 5, 8, 16} (the compile-time engine also composite last stages
+// 6, 10, 12, 20, 24) (a Stockham auto-sort decimation-in-time ordering, so
 // no bit reversal pass is needed).  Each thread holds E elements in registers;
 // thread t of a segment owns indices t + Tseg*s (s < E, Tseg = L/E) both on
 // entry and on exit, so global loads and stores are coalesced and a forward
@@ -163,6 +164,82 @@ __device__ __forceinline__ void dft16(cx<T> *b) {
   }
 }
 
+// cos / sin (2 pi m / R), m < R, for the composite last-stage radices (20
+// digits; rational multiples of pi)
+template <int R>
+struct RootsR;
+template <>
+struct RootsR<6> {
+  static constexpr double c[6] = {1.0000000000000000000, 0.50000000000000000000, -0.50000000000000000000, -1.0000000000000000000, -0.50000000000000000000, 0.50000000000000000000};
+  static constexpr double s[6] = {0.0, 0.86602540378443864676, 0.86602540378443864676, 0.0, -0.86602540378443864676, -0.86602540378443864676};
+};
+template <>
+struct RootsR<10> {
+  static constexpr double c[10] = {1.0000000000000000000, 0.80901699437494742410, 0.30901699437494742410, -0.30901699437494742410, -0.80901699437494742410, -1.0000000000000000000, -0.80901699437494742410, -0.30901699437494742410, 0.30901699437494742410, 0.80901699437494742410};
+  static constexpr double s[10] = {0.0, 0.58778525229247312917, 0.95105651629515357212, 0.95105651629515357212, 0.58778525229247312917, 0.0, -0.58778525229247312917, -0.95105651629515357212, -0.95105651629515357212, -0.58778525229247312917};
+};
+template <>
+struct RootsR<12> {
+  static constexpr double c[12] = {1.0000000000000000000, 0.86602540378443864676, 0.50000000000000000000, 0.0, -0.50000000000000000000, -0.86602540378443864676, -1.0000000000000000000, -0.86602540378443864676, -0.50000000000000000000, 0.0, 0.50000000000000000000, 0.86602540378443864676};
+  static constexpr double s[12] = {0.0, 0.50000000000000000000, 0.86602540378443864676, 1.0000000000000000000, 0.86602540378443864676, 0.50000000000000000000, 0.0, -0.50000000000000000000, -0.86602540378443864676, -1.0000000000000000000, -0.86602540378443864676, -0.50000000000000000000};
+};
+template <>
+struct RootsR<20> {
+  static constexpr double c[20] = {1.0000000000000000000, 0.95105651629515357212, 0.80901699437494742410, 0.58778525229247312917, 0.30901699437494742410, 0.0, -0.30901699437494742410, -0.58778525229247312917, -0.80901699437494742410, -0.95105651629515357212, -1.0000000000000000000, -0.95105651629515357212, -0.80901699437494742410, -0.58778525229247312917, -0.30901699437494742410, 0.0, 0.30901699437494742410, 0.58778525229247312917, 0.80901699437494742410, 0.95105651629515357212};
+  static constexpr double s[20] = {0.0, 0.30901699437494742410, 0.58778525229247312917, 0.80901699437494742410, 0.95105651629515357212, 1.0000000000000000000, 0.95105651629515357212, 0.80901699437494742410, 0.58778525229247312917, 0.30901699437494742410, 0.0, -0.30901699437494742410, -0.58778525229247312917, -0.80901699437494742410, -0.95105651629515357212, -1.0000000000000000000, -0.95105651629515357212, -0.80901699437494742410, -0.58778525229247312917, -0.30901699437494742410};
+};
+template <>
+struct RootsR<24> {
+  static constexpr double c[24] = {1.0000000000000000000, 0.96592582628906828675, 0.86602540378443864676, 0.70710678118654752440, 0.50000000000000000000, 0.25881904510252076235, 0.0, -0.25881904510252076235, -0.50000000000000000000, -0.70710678118654752440, -0.86602540378443864676, -0.96592582628906828675, -1.0000000000000000000, -0.96592582628906828675, -0.86602540378443864676, -0.70710678118654752440, -0.50000000000000000000, -0.25881904510252076235, 0.0, 0.25881904510252076235, 0.50000000000000000000, 0.70710678118654752440, 0.86602540378443864676, 0.96592582628906828675};
+  static constexpr double s[24] = {0.0, 0.25881904510252076235, 0.50000000000000000000, 0.70710678118654752440, 0.86602540378443864676, 0.96592582628906828675, 1.0000000000000000000, 0.96592582628906828675, 0.86602540378443864676, 0.70710678118654752440, 0.50000000000000000000, 0.25881904510252076235, 0.0, -0.25881904510252076235, -0.50000000000000000000, -0.70710678118654752440, -0.86602540378443864676, -0.96592582628906828675, -1.0000000000000000000, -0.96592582628906828675, -0.86602540378443864676, -0.70710678118654752440, -0.50000000000000000000, -0.25881904510252076235};
+};
+
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void dftR(cx<T> *b);
+
+// Twiddles w_R^{n2 k1} of the composite DFT below, n2 = N2.., k1 = K1..
+// (compile-time indices, so every constant folds).
+template <int A, int B, int N2, int K1, bool INV, typename T>
+__device__ __forceinline__ void ab_twiddle(cx<T> (&y)[B][A]) {
+  if constexpr (N2 < B) {
+    if constexpr (K1 < A) {
+      if constexpr (N2 > 0 && K1 > 0) {
+        constexpr int m = (N2 * K1) % (A * B);
+        constexpr double c = RootsR<A * B>::c[m], s = RootsR<A * B>::s[m];
+        y[N2][K1] = crot<INV>(y[N2][K1], T(c), T(s));
+      }
+      ab_twiddle<A, B, N2, K1 + 1, INV>(y);
+    } else {
+      ab_twiddle<A, B, N2 + 1, 0, INV>(y);
+    }
+  }
+}
+
+// R = A B point DFT (A a power of two, B = 3 or 5) by one Cooley-Tukey split:
+// with n = B n1 + n2 and k = k1 + A k2,
+//   X_{k1 + A k2} = sum_{n2} w_B^{n2 k2} w_R^{n2 k1} sum_{n1} b_{B n1 + n2} w_A^{n1 k1},
+// i.e. B DFTs of length A, the twiddles w_R^{n2 k1}, A DFTs of length B.
+template <int A, int B, bool INV, typename T>
+__device__ __forceinline__ void dft_ab(cx<T> *b) {
+  cx<T> y[B][A];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) y[n2][n1] = b[B * n1 + n2];
+    dftR<A, INV>(y[n2]);
+  }
+  ab_twiddle<A, B, 1, 1, INV>(y);
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    cx<T> z[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) z[n2] = y[n2][k1];
+    dftR<B, INV>(z);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) b[k1 + A * k2] = z[k2];
+  }
+}
+
 template <int R, bool INV, typename T>
 __device__ __forceinline__ void dftR(cx<T> *b) {
   if constexpr (R == 2) dft2<INV>(b);
@@ -171,6 +248,11 @@ __device__ __forceinline__ void dftR(cx<T> *b) {
   else if constexpr (R == 5) dft5<INV>(b);
   else if constexpr (R == 8) dft8<INV>(b);
   else if constexpr (R == 16) dft16<INV>(b);
+  else if constexpr (R == 6) dft_ab<2, 3, INV>(b);
+  else if constexpr (R == 10) dft_ab<2, 5, INV>(b);
+  else if constexpr (R == 12) dft_ab<4, 3, INV>(b);
+  else if constexpr (R == 20) dft_ab<4, 5, INV>(b);
+  else if constexpr (R == 24) dft_ab<8, 3, INV>(b);
 }
 
 // ------------------------------------------------------------ shared exchange
@@ -189,7 +271,19 @@ __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
 template <typename T, int R>
 __device__ __forceinline__ void apply_twiddles(cx<T> *b, const cx<T> *__restrict__ tw, int step) {
   const cx<T> w1 = tw[step];
-  if constexpr (R == 2) {
+  if constexpr (R == 6 || R == 10 || R == 12 || R == 20 || R == 24) {
+    // composite radices: w^r read from the table for powers of two r, the
+    // others as the product of the highest power of two below r and the rest
+    cx<T> w[R];
+    w[1] = w1;
+#pragma unroll
+    for (int r = 2; r < R; ++r) {
+      const int hb = r >= 16 ? 16 : (r >= 8 ? 8 : (r >= 4 ? 4 : 2));
+      w[r] = r == hb ? tw[r * step] : cmul(w[hb], w[r - hb]);
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) b[r] = cmul(b[r], w[r]);
+  } else if constexpr (R == 2) {
     b[1] = cmul(b[1], w1);
   } else {
     const cx<T> w2 = tw[2 * step];
@@ -320,14 +414,21 @@ __device__ __forceinline__ void fft_run(cx<T> (&v)[E], cx<T> *sm, XLayout lay, b
 // For lengths L = m 2^k (m in {1, 3, 5}) and tiles E = m 2^j the stage
 // radices, the running product Ns and every index stride are compile-time
 // constants, so the shared memory addresses reduce to a per-thread base plus
-// immediate offsets.  Same stage sequence and arithmetic as fft_run with the
-// plan of radix_plan: power-of-two radices, largest dividing E first, then
-// the odd radix m as the last stage.  Ns = product of the earlier radices and
-// Tseg = L/E are therefore powers of two at every stage.
+// immediate offsets.  Stages: power-of-two radices, largest dividing E
+// first, as in fft_run with the plan of radix_plan (identical for m = 1); for
+// m = 3, 5 the last stage takes the whole remaining factor m 2^j once it
+// divides E (a composite radix 6, 10, 12, 20 or 24 in registers: one
+// exchange fewer than the runtime plan's separate 2^j and m stages).
+// Ns = product of the earlier radices and Tseg = L/E are therefore powers of
+// two at every stage.
 namespace ct {
 constexpr int first_radix(int E) { return E % 16 == 0 ? 16 : (E % 8 == 0 ? 8 : (E % 4 == 0 ? 4 : 2)); }
+constexpr int odd_of(int x) { return x % 2 == 0 ? odd_of(x / 2) : x; }
 constexpr int pick(int rem, int E) {
   if (rem == 3 || rem == 5) return rem;  // the odd stage, last
+  // the rest fits the tile and carries the odd factor: one composite stage
+  // of radix rem = m 2^j (6, 10, 12, 20 or 24), last
+  if (odd_of(rem) != 1 && E % rem == 0) return rem;
   int r = first_radix(E);
   while (rem % r) r >>= 1;
   return r;
