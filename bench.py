@@ -223,18 +223,18 @@ def cpu_baseline(u0, lx, ly, D, times, gpu_out=None, n_snap=None):
 # for the CUDA sources they were taken on: any change to the sources makes the
 # reported traffic null until a new capture.
 # (workload, kernel class) -> {"bytes": DRAM bytes per launch, "sources_sha256": digest of csrc/}
-_SRC = "55e513f8bf32a898b28a1d1dfd4a63323bed5366061d8afd258730c160f246bb"
+_SRC = "40b891cdd74796c97d907071010876e0d4d3a4b6bbe4f795d4a1a1a4b04eedd3"
 TRAFFIC_CAPTURES = {
     # profiles/k_batch_diffusion_1024.md
-    ("diffusion_1024", "batch"): {"bytes": 169_153_792 + 783_524_352, "sources_sha256": _SRC},
+    ("diffusion_1024", "batch"): {"bytes": 168_669_952 + 784_116_992, "sources_sha256": _SRC},
     # profiles/poisson_4096_pass_kernels.md
-    ("poisson_4096", "row_r2c"): {"bytes": 67_154_944 + 20_872_960, "sources_sha256": _SRC},
-    ("poisson_4096", "column"): {"bytes": 67_263_488 + 4_386_304, "sources_sha256": _SRC},
-    ("poisson_4096", "row_c2r"): {"bytes": 67_193_088 + 13_507_328, "sources_sha256": _SRC},
+    ("poisson_4096", "row_r2c"): {"bytes": 67_155_200 + 20_592_640, "sources_sha256": _SRC},
+    ("poisson_4096", "column"): {"bytes": 67_234_816 + 4_069_632, "sources_sha256": _SRC},
+    ("poisson_4096", "row_c2r"): {"bytes": 67_198_720 + 13_627_648, "sources_sha256": _SRC},
     # profiles/wave_4096_snapshots_and_batch_mix_traffic.md
-    ("wave_4096_snapshots", "column"): {"bytes": 67_277_568 + 8_474_112, "sources_sha256": _SRC},
+    ("wave_4096_snapshots", "column"): {"bytes": 67_242_240 + 8_427_520, "sources_sha256": _SRC},
     # both launches of the batch: the persistent one and the small problems' one
-    ("batch_mix_512", "batch"): {"bytes": 4_147_081_216 + 4_491_426_304 + 13_424_384 + 48_640,
+    ("batch_mix_512", "batch"): {"bytes": 4_151_266_816 + 4_488_077_568 + 13_422_592 + 57_344,
                                  "sources_sha256": _SRC},
 }
 
